@@ -1,0 +1,257 @@
+"""Seeded synthetic workloads shaped like the test cases of arXiv:1910.13918 (Sec. III).
+
+This module is the input generator shared by the CUDA path, the tests, the benchmark and the
+oracle.  It holds grid sizes, time steps, relaxation times and initial macroscopic fields as
+functions of vertex coordinates -- and none of the method's arithmetic (no velocity set,
+equilibrium, interpolation or collision).  Each side evaluates the initial fields on its own
+vertex coordinates.
+
+Parameter recipe (readings of the paper where it is silent):
+* time step from CFL 0.5 on the mean vertex spacing h = L / (cells * p) with respect to the
+  largest D2Q25 speed |c|max = sqrt(2 (5 + sqrt 10)) = 4.0404 (Euclidean);
+* Taylor-Green vortex: U0 = Ma (c_s = 1), nu = U0 * 2 pi / Re, tau = nu / dt + 1/2 (Sec. II.D),
+  p = 1 + (rho U0^2 / 4)(cos 2x + cos 2y), rho = 1, T = p / rho;
+* Sod (Sec. III.C) and 2D Riemann (Sec. III.D) use the paper's relaxation times 1.518 and
+  1.94815; T = p / rho with R = 1;
+* shock-vortex (Sec. III.E): region A (x < 0.5) rho = 1, P = 1/gamma, u = 1.2 (Ma_A = 1.2 with
+  c_A = 1); region B from the Rankine-Hugoniot relations; an isentropic vortex of radius 0.075,
+  Ma_v = 0.25, with the radial-equilibrium exponent Ma_v^2; nu from Re = c_A R / nu = 400;
+* gamma = 1.4 everywhere, so C_v = R / (gamma - 1) = 2.5.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+GAMMA = 1.4
+CV = 1.0 / (GAMMA - 1.0)             # 2.5
+C_MAX = math.sqrt(2.0 * (5.0 + math.sqrt(10.0)))  # largest D2Q25 speed, 4.0404
+
+PERIODIC = 0
+ZERO_GRADIENT = 1
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx_cells: int
+    ny_cells: int
+    order: int
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    bc_x: int
+    bc_y: int
+    dt: float
+    tau: float
+    steps: int
+    kind: str                      # which initial field generator
+    map_a: float = 0.0             # sine-map amplitude (0: uniform grid)
+    cv: float = CV
+    nodes: str = "glc"
+    seed: int = 0
+    extra: dict = dataclasses.field(default_factory=dict)
+
+    # vertex counts: periodic axes have cells * p vertices, zero-gradient ones cells * p + 1
+    @property
+    def nx(self):
+        return self.nx_cells * self.order + (0 if self.bc_x == PERIODIC else 1)
+
+    @property
+    def ny(self):
+        return self.ny_cells * self.order + (0 if self.bc_y == PERIODIC else 1)
+
+    @property
+    def n_vertices(self):
+        return self.nx * self.ny
+
+    @property
+    def updates_per_step(self):
+        return self.n_vertices * 25 * 2
+
+    def fields(self, x, y, perturb=False):
+        """Initial (rho, u, v, T) on vertex coordinates x, y (arrays of equal shape, float64)."""
+        rho, u, v, T = _GENERATORS[self.kind](self, np.asarray(x, np.float64),
+                                              np.asarray(y, np.float64))
+        if perturb:
+            rng = np.random.default_rng(20191031 + self.seed)
+            rho = rho * (1.0 + 1e-4 * rng.standard_normal(rho.shape))
+            umax = max(float(np.max(np.abs(u))), float(np.max(np.abs(v))), 1e-3)
+            u = u + 1e-4 * umax * rng.standard_normal(u.shape)
+            v = v + 1e-4 * umax * rng.standard_normal(v.shape)
+            T = T * (1.0 + 1e-4 * rng.standard_normal(T.shape))
+        return rho, u, v, T
+
+    def resized(self, nx_cells, ny_cells, steps=None, dt=None):
+        """Same physics on another grid; the time step follows the CFL rule unless given."""
+        w = dataclasses.replace(self, nx_cells=nx_cells, ny_cells=ny_cells)
+        if dt is None:
+            dt = cfl_dt(w)
+        ratio = dt / self.dt
+        nu = (self.tau - 0.5) * self.dt
+        w.dt = dt
+        w.tau = nu / dt + 0.5
+        w.steps = steps if steps is not None else max(1, int(round(self.steps / ratio)))
+        return w
+
+
+def cfl_dt(w: Workload, cfl=0.5):
+    hx = (w.x1 - w.x0) / (w.nx_cells * w.order)
+    hy = (w.y1 - w.y0) / (w.ny_cells * w.order)
+    return cfl * min(hx, hy) / C_MAX
+
+
+# ---------------------------------------------------------------------------------------------
+# initial fields
+# ---------------------------------------------------------------------------------------------
+def _tgv(w, x, y):
+    U0 = w.extra["U0"]
+    rho = np.ones_like(x)
+    u = U0 * np.sin(x) * np.cos(y)
+    v = -U0 * np.cos(x) * np.sin(y)
+    p = 1.0 + rho * U0 ** 2 / 4.0 * (np.cos(2 * x) + np.cos(2 * y))
+    return rho, u, v, p / rho
+
+
+def _sod(w, x, y):
+    left = x < 0.5
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    z = np.zeros_like(x)
+    return rho, z.copy(), z.copy(), p / rho
+
+
+RIEMANN_STATES = {  # (rho, u, v, p) per quadrant, interfaces at x = y = 0.8
+    "NE": (1.5, 0.0, 0.0, 1.5),
+    "NW": (0.5323, 1.206, 0.0, 0.3),
+    "SW": (0.138, 1.206, 1.206, 0.029),
+    "SE": (0.5323, 0.0, 1.206, 0.3),
+}
+
+
+def _riemann(w, x, y):
+    east = x >= 0.8
+    north = y >= 0.8
+    out = [np.zeros_like(x) for _ in range(4)]
+    for key, mask in (("NE", east & north), ("NW", ~east & north),
+                      ("SW", ~east & ~north), ("SE", east & ~north)):
+        st = RIEMANN_STATES[key]
+        for k in range(4):
+            out[k] = np.where(mask, st[k], out[k])
+    rho, u, v, p = out
+    return rho, u, v, p / rho
+
+
+def rankine_hugoniot(mach, gamma=GAMMA):
+    """Density ratio, pressure ratio and downstream Mach number of a normal shock."""
+    m2 = mach * mach
+    rho_ratio = (gamma + 1) * m2 / ((gamma - 1) * m2 + 2)
+    p_ratio = 1 + 2 * gamma / (gamma + 1) * (m2 - 1)
+    mach_b = math.sqrt(((gamma - 1) * m2 + 2) / (2 * gamma * m2 - (gamma - 1)))
+    return rho_ratio, p_ratio, mach_b
+
+
+def _svi(w, x, y):
+    g = GAMMA
+    ex = w.extra
+    ma_a, ma_v, radius = ex["Ma_A"], ex["Ma_v"], ex["radius"]
+    xc, yc, xs = ex["xc"], ex["yc"], ex["x_shock"]
+    rho_r, p_r, _ = rankine_hugoniot(ma_a)
+    pA = 1.0 / g
+    uA = ma_a * 1.0                        # c_A = sqrt(gamma pA / rhoA) = 1
+    region_a = x < xs
+    rho = np.where(region_a, 1.0, rho_r)
+    p = np.where(region_a, pA, pA * p_r)
+    u = np.where(region_a, uA, uA / rho_r)
+    v = np.zeros_like(x)
+    # isentropic vortex in region A
+    dx, dy = x - xc, y - yc
+    r2 = (dx * dx + dy * dy) / radius ** 2
+    env = np.exp(0.5 * (1.0 - r2))
+    base = 1.0 - 0.5 * (g - 1) * ma_v ** 2 * np.exp(1.0 - r2)
+    rho_v = base ** (1.0 / (g - 1))
+    p_v = pA * base ** (g / (g - 1))
+    rho = np.where(region_a, rho_v, rho)
+    p = np.where(region_a, p_v, p)
+    u = np.where(region_a, uA - ma_v * env * dy / radius, u)
+    v = np.where(region_a, ma_v * env * dx / radius, v)
+    return rho, u, v, p / rho
+
+
+_GENERATORS = {"tgv": _tgv, "sod": _sod, "riemann": _riemann, "svi": _svi}
+
+
+def svi_envelope(w: Workload, x, y):
+    ex = w.extra
+    r2 = ((x - ex["xc"]) ** 2 + (y - ex["yc"]) ** 2) / ex["radius"] ** 2
+    return np.exp(0.5 * (1.0 - r2))
+
+
+def svi_directions(w: Workload, x, y, count=16):
+    """Seeded random control directions (du, dv) for finite-difference checks of the gradient."""
+    env = svi_envelope(w, x, y)
+    out = []
+    for s in range(count):
+        rng = np.random.default_rng(s)
+        out.append((rng.standard_normal(x.shape) * env, rng.standard_normal(x.shape) * env))
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
+# the five workloads
+# ---------------------------------------------------------------------------------------------
+def _tgv_workload(name, cells, p, ma, re, steps, seed):
+    L = 2 * math.pi
+    w = Workload(name, cells, cells, p, 0.0, L, 0.0, L, PERIODIC, PERIODIC, 1.0, 1.0, steps,
+                 "tgv", seed=seed, extra={"U0": ma})
+    w.dt = cfl_dt(w)
+    nu = ma * L / re
+    w.tau = nu / w.dt + 0.5
+    return w
+
+
+def tgv16():
+    """Taylor-Green vortex, 16x16 cells, p = 2 (32x32 vertices), Ma 0.1, Re 100, 100 steps."""
+    return _tgv_workload("tgv16_p2", 16, 2, 0.1, 100.0, 100, 1)
+
+
+def tgv256():
+    """Taylor-Green vortex, 256x256 cells, p = 4 (1024x1024 vertices), Ma 0.3, Re 1000."""
+    return _tgv_workload("tgv256_p4", 256, 4, 0.3, 1000.0, 1000, 2)
+
+
+def sod():
+    """Sod tube strip [0,1]x[0,4/4096], 4096x4 cells, p = 2, tau 1.518, t = 0.2."""
+    w = Workload("sod4096_p2", 4096, 4, 2, 0.0, 1.0, 0.0, 4.0 / 4096, ZERO_GRADIENT, PERIODIC,
+                 1.0, 1.518, 1, "sod", seed=3)
+    n = int(round(0.2 / cfl_dt(w)))
+    w.dt = 0.2 / n
+    w.steps = n
+    return w
+
+
+def riemann():
+    """2D Riemann problem [0,1]^2, 1024x1024 cells, p = 3, tau 1.94815, t = 0.3."""
+    w = Workload("riemann1024_p3", 1024, 1024, 3, 0.0, 1.0, 0.0, 1.0, ZERO_GRADIENT,
+                 ZERO_GRADIENT, 1.0, 1.94815, 1, "riemann", seed=4)
+    n = int(round(0.3 / cfl_dt(w)))
+    w.dt = 0.3 / n
+    w.steps = n
+    return w
+
+
+def svi():
+    """Shock-vortex interaction on the sine-mapped grid [0,2]x[0,1], 512x256 cells, p = 2."""
+    radius = 0.075
+    nu = 1.0 * radius / 400.0
+    dt = 3.0e-3
+    return Workload("svi512x256_p2_mapped", 512, 256, 2, 0.0, 2.0, 0.0, 1.0, ZERO_GRADIENT,
+                    PERIODIC, dt, nu / dt + 0.5, 200, "svi", map_a=0.05, seed=5,
+                    extra={"Ma_A": 1.2, "Ma_v": 0.25, "radius": radius, "xc": 0.25, "yc": 0.5,
+                           "x_shock": 0.5, "x_objective": 1.5, "checkpoint_every": 20})
+
+
+ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann, "svi": svi}

@@ -1,0 +1,105 @@
+"""Physics pins of the oracle: closed-form flows and textbook solutions (no GPU needed)."""
+import math
+
+import numpy as np
+
+from oracle import riemann
+from oracle import sllbm as o
+from paper_1910_13918_gb300 import workloads as W
+
+
+def test_exact_riemann_solver_sod_star_state():
+    """Star state of Sod's problem: the textbook values p* = 0.30313, u* = 0.92745."""
+    ps, us = riemann.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4)
+    assert abs(ps - 0.30313) < 1e-5 and abs(us - 0.92745) < 1e-5
+    # Rankine-Hugoniot mass flux continuity across the right-moving shock
+    s = np.linspace(-2, 2, 4001)
+    rho, u, p = riemann.sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, s)
+    g = 1.4
+    shock = 0.0 + math.sqrt(g * 0.1 / 0.125) * math.sqrt((g + 1) / (2 * g) * ps / 0.1 + (g - 1) / (2 * g))
+    r_star = rho[np.searchsorted(s, shock) - 2]
+    assert abs(r_star * (us - shock) - 0.125 * (0.0 - shock)) < 1e-12
+
+
+def test_rankine_hugoniot_downstream_mach():
+    """Ma_B = 0.842 behind a Ma 1.2 normal shock (Sec. III.E)."""
+    _, _, mb = W.rankine_hugoniot(1.2)
+    assert abs(mb - 0.84217) < 1e-5
+
+
+def test_taylor_green_viscous_decay():
+    """Kinetic energy decays as exp(-4 nu t) with nu = (tau - 1/2) c_s^2 theta dt (Sec. II.F)."""
+    base = W.tgv16()
+    cells, p, steps = 8, 4, 50
+    ax = o.Axis(cells, p, 0.0, 2 * math.pi, True)
+    ay = o.Axis(cells, p, 0.0, 2 * math.pi, True)
+    grid = o.Grid(ax, ay)
+    X, Y = grid.coords()
+    A = grid.vertex_weights()
+    f, g = o.initial_state(*base.fields(X, Y), base.cv)
+    dep = o.Departures(grid, base.dt)
+
+    def ke(f, g):
+        r, u, _ = o.macroscopic(f, g, base.cv)
+        return np.sum(A * r * (u ** 2).sum(-1))
+
+    k0 = ke(f, g)
+    f, g = o.run(f, g, dep, base.tau, base.cv, steps)
+    nu = (base.tau - 0.5) * base.dt
+    nu_eff = -math.log(ke(f, g) / k0) / (4 * steps * base.dt)
+    assert abs(nu_eff / nu - 1) < 0.03, nu_eff / nu
+
+
+def test_periodic_mass_drift_small():
+    """Mass is conserved up to interpolation loss on a periodic grid (cf. Sec. III.E, p = 2)."""
+    base = W.tgv16()
+    ax = o.Axis(16, 2, 0.0, 2 * math.pi, True)
+    ay = o.Axis(16, 2, 0.0, 2 * math.pi, True)
+    grid = o.Grid(ax, ay)
+    X, Y = grid.coords()
+    A = grid.vertex_weights()
+    f, g = o.initial_state(*base.fields(X, Y), base.cv)
+    m0, e0 = o.mass_energy(f, g, A)
+    f, g = o.run(f, g, o.Departures(grid, base.dt), base.tau, base.cv, 20)
+    m1, e1 = o.mass_energy(f, g, A)
+    assert abs(m1 / m0 - 1) < 1e-6 and abs(e1 / e0 - 1) < 1e-5
+
+
+def test_sod_shock_tube_against_exact_solution():
+    """Sod tube (Sec. III.C, tau = 1.518) at t = 0.2 on 128 p = 2 cells: L1(rho) small."""
+    cells, dt, tau = 128, 2e-3, 1.518
+    ax = o.Axis(cells, 2, 0.0, 1.0, False)
+    ay = o.Axis(1, 2, 0.0, 1.0 / cells, True)
+    grid = o.Grid(ax, ay)
+    X, Y = grid.coords()
+    w = W.sod()
+    f, g = o.initial_state(*w.fields(X, Y), w.cv)
+    f, g = o.run(f, g, o.Departures(grid, dt), tau, w.cv, int(round(0.2 / dt)))
+    rho, u, th = o.macroscopic(f, g, w.cv)
+    re, ue, pe = riemann.sample((1, 0, 1), (0.125, 0, 0.1), 1.4, (X[0] - 0.5) / 0.2)
+    err = np.mean(np.abs(rho[0] - re))
+    assert err < 0.012, err
+    # plateau between contact and shock at the exact star density
+    mid = (X[0] > 0.75) & (X[0] < 0.82)
+    assert np.max(np.abs(rho[0][mid] - 0.26557)) < 0.02
+
+
+def test_stationary_shock_stays():
+    """A Rankine-Hugoniot shock (Ma 1.2) in a flow through the domain stays in place."""
+    rr, pr, _ = W.rankine_hugoniot(1.2)
+    g = 1.4
+    cells = 64
+    ax = o.Axis(cells, 2, 0.0, 1.0, False)
+    ay = o.Axis(1, 2, 0.0, 1.0 / cells, True)
+    grid = o.Grid(ax, ay)
+    X, _ = grid.coords()
+    a = X < 0.5
+    rho = np.where(a, 1.0, rr)
+    u = np.where(a, 1.2, 1.2 / rr)
+    p = np.where(a, 1 / g, pr / g)
+    f, g_ = o.initial_state(rho, u, 0 * u, p / rho, 2.5)
+    f, g_ = o.run(f, g_, o.Departures(grid, 2e-3), 0.9, 2.5, 100)
+    r1, _, _ = o.macroscopic(f, g_, 2.5)
+    mid = 0.5 * (1 + rr)
+    x_shock = X[0][np.argmin(np.abs(r1[0] - mid))]
+    assert abs(x_shock - 0.5) < 2.0 / (cells * 2), x_shock
