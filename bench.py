@@ -1,0 +1,312 @@
+"""Benchmark of the fused SLLBM step (GVUPS = vertex x velocity x population updates per second).
+
+Default workload: the 1024x1024-vertex Taylor-Green vortex at order p = 4 (256x256 cells, D2Q25,
+f and g populations), FP32 deviation storage, one fused kernel launch per step.  The state
+(2 x 210 MB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload tgv256|riemann|sod|svi|tgv16] [--prec f32|bf16|f64]
+
+Under torchrun every rank runs an independent replica on its own GPU (the method needs no
+exchange between replicas); rank 0 prints one JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GVUPS (vertex x velocity x population updates/s), fused FP32 SLLBM step"
+UNIT = "GVUPS"
+
+# DRAM traffic (read + write bytes per launch) of the step kernel from an ncu capture, keyed by
+# (kernel source digest, workload, precision); reported as null once the kernel source changes.
+NCU_TRAFFIC = {}
+
+
+def _kernel_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1910_13918_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, n in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(name):
+    from paper_1910_13918_gb300 import workloads as W
+    return W.ALL[name]()
+
+
+def _workload_desc(w):
+    return (f"{w.name}: {w.nx}x{w.ny} vertices ({w.nx_cells}x{w.ny_cells} cells, p={w.order}), "
+            f"D2Q25, f and g populations, dt={w.dt:.6g}, tau={w.tau:.6g}")
+
+
+# -------------------------------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# -------------------------------------------------------------------------------------------------
+def oracle_sample_step_time(w, rows=16):
+    """Seconds for one oracle step on the first `rows` vertex rows of the workload, and the
+    number of vertices in that sample.  Initial state evaluated only where the stencils reach."""
+    import numpy as np
+    from oracle import sllbm as o
+    ax = o.Axis(w.nx_cells, w.order, w.x0, w.x1, w.bc_x == 0, w.nodes)
+    ay = o.Axis(w.ny_cells, w.order, w.y0, w.y1, w.bc_y == 0, w.nodes)
+    grid = o.Grid(ax, ay, o.SineMap(w.map_a) if w.map_a else None)
+    X, Y = grid.coords()
+    verts = np.arange(min(rows, grid.ny) * grid.nx)
+    # support of the stencils of the sample (setup, not timed)
+    dep0 = o.Departures(grid, w.dt, verts)
+    keys = []
+    for i in range(25):
+        for b in range(grid.p + 1):
+            for a in range(grid.p + 1):
+                keys.append(ay.vertex_of(dep0.cy[i], b) * grid.nx + ax.vertex_of(dep0.cx[i], a))
+    keys = np.unique(np.concatenate(keys))
+    fields = [np.asarray(F).reshape(-1)[keys] for F in w.fields(X, Y)]
+    f0, g0 = o.initial_state(*fields, w.cv)
+    F = np.zeros((25, grid.ny * grid.nx))
+    G = np.zeros((25, grid.ny * grid.nx))
+    F[:, keys] = f0
+    G[:, keys] = g0
+    F = F.reshape(25, grid.ny, grid.nx)
+    G = G.reshape(25, grid.ny, grid.nx)
+    t = time.perf_counter()
+    dep = o.Departures(grid, w.dt, verts)          # the oracle recomputes departures every step
+    fpre = o.stream(F, dep)
+    gpre = o.stream(G, dep)
+    o.collide(fpre, gpre, w.tau, w.cv)
+    return time.perf_counter() - t, len(verts)
+
+
+def cpu_baseline(w):
+    el, nv = oracle_sample_step_time(w)
+    return {"value": nv * 50 / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle step on the first 16 vertex rows ({nv} vertices) of {w.name}, "
+                      f"{el:.2f} s, numpy float64 single thread"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    w = _workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample_step_time(w, rows=4)
+    times, nv = [], 0
+    for _ in range(args.steps):
+        el, nv = oracle_sample_step_time(w, rows=4)
+        times.append(el)
+    tot = sum(times)
+    value = nv * 50 * len(times) / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": _workload_desc(w), "sample_vertices": nv},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: one oracle step on the first 4 vertex rows "
+                                       f"({nv} vertices) of {w.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# -------------------------------------------------------------------------------------------------
+# GPU arm
+# -------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1910_13918_gb300.sllbm import SLLBM
+    w = _workload(args.workload)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = SLLBM.from_workload(w, prec=args.prec, stream=stream)
+        s.precompute()
+        x, y = (t.cpu().numpy() for t in s.coords())
+        fields = w.fields(x, y)
+        s.init(*fields)
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clocks = sampler.stop()
+        ms = e0.elapsed_time(e1)
+        m = s.moments()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    updates = w.updates_per_step
+    value = updates * args.steps * ws / (ms_max * 1e-3) / 1e9
+
+    # end to end through the host-buffer entry point: copy state in, one step, copy state out
+    e2e = None
+    if not args.no_e2e:
+        nb = s.state_bytes
+        hin = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        hout = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        st = s.get_state()
+        hin.copy_(st.view(torch.uint8).reshape(-1).cpu())
+        a_in, a_out = hin.numpy(), hout.numpy()
+        s.step_host(a_in, a_out, 1)
+        k = max(3, min(args.steps, 20))
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            s.step_host(a_in, a_out, 1)
+        el = time.perf_counter() - t0
+        te = torch.tensor([el], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        el = float(te.item())
+        e2e = {"value": updates * k * ws / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb,
+               "api": "sllbm_step_host (pinned host state in, 1 step, state out)"}
+
+    if rank == 0:
+        peaks, src = _peaks()
+        bytes_per_update = {"f32": 8, "bf16": 4, "f64": 16}[args.prec]
+        alg_bytes = updates * bytes_per_update
+        achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        traffic = NCU_TRAFFIC.get((_kernel_digest(), w.name, args.prec))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "bf16": "f32 (bf16 storage)", "f64": "f64"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": _workload_desc(w), "kernel": s.kernel_name,
+                       "n_vertices": w.n_vertices, "updates_per_step": updates,
+                       "l2": "state 2 x %.0f MB > 129 MB L2, no flush" % (s.state_bytes / 1e6),
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"hbm_gbs of {src} peaks",
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "clocks": clocks,
+            "e2e": e2e,
+            "gpu_launches": args.steps * s.launches_per_step,
+            "mass_after": m["mass"],
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tgv256")
+    ap.add_argument("--prec", default="f32", choices=["f32", "bf16", "f64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,681 @@
+// C ABI of the SLLBM library (include/sllbm.h): context, buffers, host-side set-up (velocity set,
+// support points, Gauss-Legendre rule, transposed stencils) and dispatch to the kernels.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sllbm.h"
+#include "kernels.h"
+
+using namespace sllbm;
+
+enum StepKernel { kKernelUniform = 0, kKernelGather = 1, kKernelPlainF64 = 2 };
+
+struct sllbm_ctx {
+  sllbm_grid_desc g;
+  sllbm_params p;
+  cudaStream_t stream = nullptr;
+  int nx = 0, ny = 0, npop = 2, P = 0, pitch = 0, store = kStoreF32, elem = 4;
+  long long nv = 0;
+  size_t plane_stride = 0;
+  AxisK ax{}, ay{};
+  MapK map{};
+  Consts cs{};
+  CollideK cp{};
+  void* state[2] = {nullptr, nullptr};
+  int cur = 0;
+  bool precomputed = false, initialized = false;
+  int kernel = kKernelGather;
+  // uniform tables
+  int *offx = nullptr, *offy = nullptr;
+  float *wx = nullptr, *wy = nullptr;
+  double *wx64 = nullptr, *wy64 = nullptr;
+  int offx_lo = 0, offx_hi = 0, offy_lo = 0, offy_hi = 0;
+  // per-(velocity, vertex) descriptors
+  int *dcx = nullptr, *dcy = nullptr;
+  float *dr = nullptr, *ds = nullptr;
+  double *dr64 = nullptr, *ds64 = nullptr;
+  // diagnostics
+  double* A = nullptr;
+  double* partials = nullptr;
+  double* sums = nullptr;
+  int* flag = nullptr;
+  // adjoint
+  bool transposed = false;
+  float* mu = nullptr;
+  int *tx_ptr = nullptr, *tx_col = nullptr, *ty_ptr = nullptr, *ty_col = nullptr;
+  float *tx_w = nullptr, *ty_w = nullptr;
+  long long* tm_ptr = nullptr;
+  int* tm_col = nullptr;
+  float* tm_w = nullptr;
+  std::vector<void*> allocations;
+  std::string err;
+};
+
+// ------------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------------
+static sllbm_status fail(sllbm_ctx* c, sllbm_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+static sllbm_status cuda_fail(sllbm_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, SLLBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(ctx, call)                                 \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+  } while (0)
+
+template <typename T>
+static sllbm_status dalloc(sllbm_ctx* c, T** ptr, size_t count) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, SLLBM_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                      " bytes failed: " + cudaGetErrorString(e));
+  }
+  c->allocations.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return SLLBM_OK;
+}
+
+#define TRY(call)                          \
+  do {                                     \
+    sllbm_status _s = (call);              \
+    if (_s != SLLBM_OK) return _s;         \
+  } while (0)
+
+// D1Q5 abscissae and weights in Table I order; he[k][a] = He_k(xi_a) / k! by the recurrence
+// He_{k+1}(x) = x He_k(x) - k He_{k-1}(x).
+static void build_consts(Consts& cs) {
+  const double s10 = sqrt(10.0);
+  const double sm = sqrt(5.0 - s10), lg = sqrt(5.0 + s10);
+  const double xi[5] = {0.0, sm, lg, -sm, -lg};
+  const double w[5] = {8.0 / 15.0, (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0,
+                       (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0};
+  for (int a = 0; a < 5; ++a) {
+    cs.xi[a] = xi[a];
+    cs.w[a] = w[a];
+    double hm1 = 0.0, h = 1.0, fact = 1.0;
+    for (int k = 0; k < 5; ++k) {
+      if (k > 0) fact *= k;
+      cs.he[k][a] = h / fact;
+      const double hn = xi[a] * h - k * hm1;
+      hm1 = h;
+      h = hn;
+    }
+    cs.xif[a] = (float)xi[a];
+    cs.wf[a] = (float)w[a];
+    for (int k = 0; k < 5; ++k) cs.hef[k][a] = (float)cs.he[k][a];
+  }
+}
+
+static void build_axis(AxisK& ax, int n_cells, int p, double lo, double hi, int periodic, int nodes) {
+  ax.n_cells = n_cells;
+  ax.p = p;
+  ax.periodic = periodic;
+  ax.nv = periodic ? n_cells * p : n_cells * p + 1;
+  ax.lo = lo;
+  ax.hi = hi;
+  ax.len = hi - lo;
+  ax.hc = (hi - lo) / n_cells;
+  const double pi = 3.141592653589793238462643383279502884;
+  for (int k = 0; k < 5; ++k) ax.nodes[k] = 0.0;
+  for (int k = 0; k <= p; ++k)  // Gauss-Lobatto-Chebyshev points (Sec. II.E) or equidistant
+    ax.nodes[k] = nodes == SLLBM_NODES_GLC ? 0.5 * (1.0 - cos(k * pi / p)) : (double)k / p;
+}
+
+// Gauss-Legendre rule with n points on [0, 1] (Newton on the Legendre recurrence).
+static void gauss_legendre01(int n, double* x, double* w) {
+  const double pi = 3.141592653589793238462643383279502884;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // 2/((1-z^2)P'^2) on [-1,1], halved for [0,1]
+  }
+}
+
+static StepArgs step_args(sllbm_ctx* c, const void* src, void* dst) {
+  StepArgs a{};
+  a.src = src;
+  a.dst = dst;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.pitch = c->pitch;
+  a.periodic_x = c->ax.periodic;
+  a.periodic_y = c->ay.periodic;
+  a.P = c->P;
+  a.nv = c->nv;
+  a.plane_stride = c->plane_stride;
+  a.offx = c->offx;
+  a.offy = c->offy;
+  a.wx = c->wx;
+  a.wy = c->wy;
+  a.wx64 = c->wx64;
+  a.wy64 = c->wy64;
+  a.dcx = c->dcx;
+  a.dcy = c->dcy;
+  a.dr = c->dr;
+  a.ds = c->ds;
+  a.dr64 = c->dr64;
+  a.ds64 = c->ds64;
+  for (int k = 0; k < 5; ++k) {
+    a.nodes[k] = c->ax.nodes[k];
+    a.nodesf[k] = (float)c->ax.nodes[k];
+  }
+  a.cs = c->cs;
+  a.cp = c->cp;
+  a.flag = c->flag;
+  a.mapped = (c->map.kind != SLLBM_MAP_IDENTITY) || (c->kernel == kKernelGather && c->dcx != nullptr);
+  a.offx_min = c->offx_lo;
+  a.offx_max = c->offx_hi;
+  a.offy_min = c->offy_lo;
+  a.offy_max = c->offy_hi;
+  return a;
+}
+
+static GeomArgs geom_args(sllbm_ctx* c) {
+  GeomArgs g{};
+  g.ax = c->ax;
+  g.ay = c->ay;
+  g.map = c->map;
+  g.cs = c->cs;
+  g.dt = c->p.dt;
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.nv = c->nv;
+  g.flag = c->flag;
+  return g;
+}
+
+// ------------------------------------------------------------------------------------------
+// API
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* sllbm_status_string(sllbm_status s) {
+  switch (s) {
+    case SLLBM_OK: return "ok";
+    case SLLBM_ERR_ARG: return "invalid argument";
+    case SLLBM_ERR_CUDA: return "CUDA error";
+    case SLLBM_ERR_OOM: return "out of memory";
+    case SLLBM_ERR_STATE: return "call order (precompute/init missing)";
+    case SLLBM_ERR_NEWTON: return "Newton inversion of the grid map failed";
+    case SLLBM_ERR_UNSTABLE: return "unstable: non-positive or non-finite density/temperature";
+    case SLLBM_ERR_UNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* sllbm_last_error(const sllbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+sllbm_status sllbm_destroy(sllbm_ctx* c) {
+  if (!c) return SLLBM_ERR_ARG;
+  for (void* p : c->allocations) cudaFree(p);
+  delete c;
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void* stream, sllbm_ctx** out) {
+  if (!g || !p || !out) return SLLBM_ERR_ARG;
+  *out = nullptr;
+  if (g->order < 1 || g->order > 4) return SLLBM_ERR_UNSUPPORTED;
+  if (p->velset != SLLBM_VEL_D2Q25_HERMITE) return SLLBM_ERR_UNSUPPORTED;
+  if (g->nx_cells < 1 || g->ny_cells < 1 || !(g->x1 > g->x0) || !(g->y1 > g->y0)) return SLLBM_ERR_ARG;
+  if ((g->bc_x != SLLBM_BC_PERIODIC && g->bc_x != SLLBM_BC_ZERO_GRADIENT) ||
+      (g->bc_y != SLLBM_BC_PERIODIC && g->bc_y != SLLBM_BC_ZERO_GRADIENT))
+    return SLLBM_ERR_ARG;
+  if (g->nodes != SLLBM_NODES_GLC && g->nodes != SLLBM_NODES_EQUIDISTANT) return SLLBM_ERR_ARG;
+  if (g->map != SLLBM_MAP_IDENTITY && g->map != SLLBM_MAP_SINE) return SLLBM_ERR_ARG;
+  if (p->prec != SLLBM_PREC_F32 && p->prec != SLLBM_PREC_BF16_STORE && p->prec != SLLBM_PREC_F64_PLAIN)
+    return SLLBM_ERR_ARG;
+  if (!(p->dt > 0.0) || !(p->tau > 0.5) || !(p->cv >= 1.0) || p->T0 != 1.0) return SLLBM_ERR_ARG;
+  if ((long long)g->nx_cells * g->order > (1 << 20) || (long long)g->ny_cells * g->order > (1 << 20))
+    return SLLBM_ERR_UNSUPPORTED;
+  sllbm_ctx* c = new (std::nothrow) sllbm_ctx();
+  if (!c) return SLLBM_ERR_OOM;
+  c->g = *g;
+  c->p = *p;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->P = g->order;
+  build_consts(c->cs);
+  build_axis(c->ax, g->nx_cells, g->order, g->x0, g->x1, g->bc_x == SLLBM_BC_PERIODIC, g->nodes);
+  build_axis(c->ay, g->ny_cells, g->order, g->y0, g->y1, g->bc_y == SLLBM_BC_PERIODIC, g->nodes);
+  c->map.kind = g->map;
+  c->map.a = g->map_param[0];
+  c->nx = c->ax.nv;
+  c->ny = c->ay.nv;
+  c->nv = (long long)c->nx * c->ny;
+  c->npop = (p->cv == 1.0) ? 1 : 2;
+  c->cp.omega = 1.0 / p->tau;
+  c->cp.cv = p->cv;
+  c->cp.K = 2.0 * p->cv - 2.0;
+  c->cp.omegaf = (float)c->cp.omega;
+  c->cp.cvf = (float)p->cv;
+  c->cp.Kf = (float)c->cp.K;
+  c->cp.npop = c->npop;
+  c->store = p->prec == SLLBM_PREC_F32 ? kStoreF32 : (p->prec == SLLBM_PREC_BF16_STORE ? kStoreBF16 : kStoreF64);
+  c->elem = c->store == kStoreF32 ? 4 : (c->store == kStoreBF16 ? 2 : 8);
+  c->pitch = (c->nx + 7) / 8 * 8;   // 16-byte aligned rows for every storage type
+  c->plane_stride = (size_t)c->ny * c->pitch;
+  sllbm_status s;
+  const size_t state_elems = (size_t)2 * kQ * c->plane_stride;
+  for (int k = 0; k < 2; ++k) {
+    void* ptr = nullptr;
+    s = dalloc(c, reinterpret_cast<char**>(&ptr), state_elems * c->elem);
+    if (s != SLLBM_OK) { std::string m = c->err; sllbm_destroy(c); (void)m; return s; }
+    c->state[k] = ptr;
+    if (cudaMemsetAsync(ptr, 0, state_elems * c->elem, c->stream) != cudaSuccess) {
+      sllbm_destroy(c);
+      return SLLBM_ERR_CUDA;
+    }
+  }
+  const int nblocks = moments_blocks(c->nv);
+  if ((s = dalloc(c, &c->A, c->nv)) != SLLBM_OK || (s = dalloc(c, &c->partials, 2 * (size_t)nblocks)) != SLLBM_OK ||
+      (s = dalloc(c, &c->sums, 2)) != SLLBM_OK || (s = dalloc(c, &c->flag, 1)) != SLLBM_OK) {
+    sllbm_destroy(c);
+    return s;
+  }
+  if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream) != cudaSuccess) {
+    sllbm_destroy(c);
+    return SLLBM_ERR_CUDA;
+  }
+  *out = c;
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_set_stream(sllbm_ctx* c, void* stream) {
+  if (!c) return SLLBM_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_grid_info(const sllbm_ctx* c, int* nx, int* ny, int* npop) {
+  if (!c) return SLLBM_ERR_ARG;
+  if (nx) *nx = c->nx;
+  if (ny) *ny = c->ny;
+  if (npop) *npop = c->npop;
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_state_bytes(const sllbm_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return SLLBM_ERR_ARG;
+  *bytes = (size_t)c->npop * kQ * c->nv * c->elem;
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_vertex_coords(sllbm_ctx* c, double* x, double* y) {
+  if (!c || !x || !y) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  CUDA_TRY(c, launch_vertex_coords(geom_args(c), x, y, c->stream));
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_vertex_weights(sllbm_ctx* c, double* A) {
+  if (!c || !A) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  if (!c->precomputed) return fail(c, SLLBM_ERR_STATE, "precompute_departures first");
+  CUDA_TRY(c, cudaMemcpyAsync(A, c->A, sizeof(double) * c->nv, cudaMemcpyDeviceToDevice, c->stream));
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
+  if (!c) return SLLBM_ERR_ARG;
+  GeomArgs g = geom_args(c);
+  const bool mapped = c->map.kind != SLLBM_MAP_IDENTITY;
+  if (!mapped) {  // per-axis tables
+    if (!c->offx) {
+      TRY(dalloc(c, &c->offx, kQ1 * (size_t)c->nx));
+      TRY(dalloc(c, &c->offy, kQ1 * (size_t)c->ny));
+      TRY(dalloc(c, &c->wx, kQ1 * (size_t)c->nx * (c->P + 1)));
+      TRY(dalloc(c, &c->wy, kQ1 * (size_t)c->ny * (c->P + 1)));
+      TRY(dalloc(c, &c->wx64, kQ1 * (size_t)c->nx * (c->P + 1)));
+      TRY(dalloc(c, &c->wy64, kQ1 * (size_t)c->ny * (c->P + 1)));
+    }
+    CUDA_TRY(c, launch_axis_tables(c->ax, c->cs, c->p.dt, c->offx, c->wx, c->wx64, c->stream));
+    CUDA_TRY(c, launch_axis_tables(c->ay, c->cs, c->p.dt, c->offy, c->wy, c->wy64, c->stream));
+    std::vector<int> ox(kQ1 * (size_t)c->nx), oy(kQ1 * (size_t)c->ny);
+    CUDA_TRY(c, cudaMemcpyAsync(ox.data(), c->offx, ox.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(oy.data(), c->offy, oy.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->offx_lo = *std::min_element(ox.begin(), ox.end());
+    c->offx_hi = *std::max_element(ox.begin(), ox.end()) + c->P;
+    c->offy_lo = *std::min_element(oy.begin(), oy.end());
+    c->offy_hi = *std::max_element(oy.begin(), oy.end()) + c->P;
+  }
+  if (c->store == kStoreF64) {
+    c->kernel = kKernelPlainF64;
+  } else if (!mapped) {
+    StepArgs a = step_args(c, nullptr, nullptr);
+    c->kernel = uniform_kernel_fits(a) ? kKernelUniform : kKernelGather;
+  } else {
+    c->kernel = kKernelGather;
+  }
+  const bool need_desc = mapped || (c->kernel == kKernelGather);
+  if (need_desc) {
+    if (!c->dcx) {
+      const size_t n = (size_t)kQ * c->nv;
+      TRY(dalloc(c, &c->dcx, n));
+      TRY(dalloc(c, &c->dcy, n));
+      TRY(dalloc(c, &c->dr, n));
+      TRY(dalloc(c, &c->ds, n));
+      TRY(dalloc(c, &c->dr64, n));
+      TRY(dalloc(c, &c->ds64, n));
+    }
+    CUDA_TRY(c, launch_descriptors(g, c->dcx, c->dcy, c->dr, c->ds, c->dr64, c->ds64, c->stream));
+  }
+  double glx[8], glw[8];
+  const int ngl = c->P + 3;
+  gauss_legendre01(ngl, glx, glw);
+  CUDA_TRY(c, launch_vertex_weights(g, glx, glw, ngl, c->A, c->stream));
+  int flag = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (flag & 2) return fail(c, SLLBM_ERR_NEWTON, "Newton inversion of the grid map did not converge");
+  c->precomputed = true;
+  c->transposed = false;
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_init_equilibrium(sllbm_ctx* c, const double* rho, const double* u, const double* v,
+                                    const double* T) {
+  if (!c || !rho || !u || !v || !T) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  if (!c->precomputed) return fail(c, SLLBM_ERR_STATE, "precompute_departures first");
+  InitArgs a{};
+  a.rho = rho;
+  a.u = u;
+  a.v = v;
+  a.T = T;
+  a.dst = c->state[c->cur];
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.pitch = c->pitch;
+  a.nv = c->nv;
+  a.plane_stride = c->plane_stride;
+  a.cs = c->cs;
+  a.cp = c->cp;
+  a.store = c->store;
+  CUDA_TRY(c, launch_init_equilibrium(a, c->stream));
+  c->initialized = true;
+  return SLLBM_OK;
+}
+
+static cudaError_t enqueue_step(sllbm_ctx* c) {
+  StepArgs a = step_args(c, c->state[c->cur], c->state[c->cur ^ 1]);
+  cudaError_t e;
+  switch (c->kernel) {
+    case kKernelUniform: e = launch_step_uniform(a, c->store, c->stream); break;
+    case kKernelPlainF64: e = launch_step_plain_f64(a, c->stream); break;
+    default: e = launch_step_gather(a, c->store, c->stream); break;
+  }
+  if (e == cudaSuccess) c->cur ^= 1;
+  return e;
+}
+
+sllbm_status sllbm_step(sllbm_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return fail(c, SLLBM_ERR_ARG, "bad arguments");
+  if (!c->precomputed || !c->initialized) return fail(c, SLLBM_ERR_STATE, "precompute and init first");
+  for (int k = 0; k < nsteps; ++k) CUDA_TRY(c, enqueue_step(c));
+  return SLLBM_OK;
+}
+
+const char* sllbm_step_kernel_name(const sllbm_ctx* c) {
+  if (!c) return "none";
+  switch (c->kernel) {
+    case kKernelUniform: return "uniform_fused";
+    case kKernelPlainF64: return "plain_f64";
+    default: return "gather";
+  }
+}
+
+int sllbm_launches_per_step(const sllbm_ctx* c) { return c ? 1 : 0; }
+
+static cudaError_t copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
+  // dense [npop][25][ny][nx] <-> pitched [npop][25][ny][pitch]
+  const size_t row = (size_t)c->nx * c->elem, prow = (size_t)c->pitch * c->elem;
+  const size_t rows = (size_t)c->npop * kQ * c->ny;
+  if (to_internal) return cudaMemcpy2DAsync(dst, prow, src, row, row, rows, kind, c->stream);
+  return cudaMemcpy2DAsync(dst, row, src, prow, row, rows, kind, c->stream);
+}
+
+sllbm_status sllbm_get_state(sllbm_ctx* c, void* dst) {
+  if (!c || !dst) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  CUDA_TRY(c, copy_state(c, dst, c->state[c->cur], false, cudaMemcpyDeviceToDevice));
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_set_state(sllbm_ctx* c, const void* src) {
+  if (!c || !src) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  CUDA_TRY(c, copy_state(c, c->state[c->cur], src, true, cudaMemcpyDeviceToDevice));
+  c->initialized = true;
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_step_host(sllbm_ctx* c, const void* in, void* out, int nsteps) {
+  if (!c || !in || !out || nsteps < 0) return fail(c, SLLBM_ERR_ARG, "bad arguments");
+  if (!c->precomputed) return fail(c, SLLBM_ERR_STATE, "precompute_departures first");
+  CUDA_TRY(c, copy_state(c, c->state[c->cur], in, true, cudaMemcpyHostToDevice));
+  c->initialized = true;
+  for (int k = 0; k < nsteps; ++k) CUDA_TRY(c, enqueue_step(c));
+  CUDA_TRY(c, copy_state(c, out, c->state[c->cur], false, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_moments(sllbm_ctx* c, float* rho, float* u, float* v, float* T, double* me) {
+  if (!c) return SLLBM_ERR_ARG;
+  if (!c->initialized) return fail(c, SLLBM_ERR_STATE, "no state");
+  MomentArgs a{};
+  a.src = c->state[c->cur];
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.pitch = c->pitch;
+  a.nv = c->nv;
+  a.plane_stride = c->plane_stride;
+  a.cs = c->cs;
+  a.cp = c->cp;
+  a.store = c->store;
+  a.A = c->precomputed ? c->A : nullptr;
+  a.rho = rho;
+  a.u = u;
+  a.v = v;
+  a.T = T;
+  a.partials = me ? c->partials : nullptr;
+  a.sums = c->sums;
+  a.flag = c->flag;
+  CUDA_TRY(c, launch_moments(a, c->stream));
+  int flag = 0;
+  if (me) CUDA_TRY(c, cudaMemcpyAsync(me, c->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (flag & 1) return fail(c, SLLBM_ERR_UNSTABLE, "non-positive or non-finite density/temperature");
+  return SLLBM_OK;
+}
+
+// ---- transposed stencils for the adjoint (host build from the FP64 tables) ----
+static sllbm_status build_axis_transpose(sllbm_ctx* c, const AxisK& ax, const int* off_dev,
+                                         const double* w_dev, int** ptr_dev, int** col_dev, float** w_out) {
+  const int n = ax.nv, P = c->P;
+  std::vector<int> off((size_t)kQ1 * n);
+  std::vector<double> w((size_t)kQ1 * n * (P + 1));
+  CUDA_TRY(c, cudaMemcpyAsync(off.data(), off_dev, off.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(w.data(), w_dev, w.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  std::vector<int> ptr((size_t)kQ1 * (n + 1), 0);
+  // count entries per (component, source vertex)
+  for (int comp = 0; comp < kQ1; ++comp)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k <= P; ++k) {
+        const int src = wrap_index(j + off[(size_t)comp * n + j] + k, n, ax.periodic);
+        ptr[(size_t)comp * (n + 1) + src + 1]++;
+      }
+  std::vector<int> start(ptr.size());
+  size_t total = 0;
+  for (int comp = 0; comp < kQ1; ++comp) {
+    int* p0 = &ptr[(size_t)comp * (n + 1)];
+    p0[0] = (int)total;
+    for (int j = 0; j < n; ++j) p0[j + 1] += p0[j];
+    total = p0[n];
+  }
+  std::vector<int> col(total);
+  std::vector<float> wt(total);
+  std::vector<int> fill(ptr.begin(), ptr.end());
+  for (int comp = 0; comp < kQ1; ++comp)
+    for (int j = 0; j < n; ++j)  // ascending target order within each row: deterministic
+      for (int k = 0; k <= P; ++k) {
+        const int src = wrap_index(j + off[(size_t)comp * n + j] + k, n, ax.periodic);
+        const int e = fill[(size_t)comp * (n + 1) + src]++;
+        col[e] = j;
+        wt[e] = (float)w[((size_t)comp * n + j) * (P + 1) + k];
+      }
+  TRY(dalloc(c, ptr_dev, ptr.size()));
+  TRY(dalloc(c, col_dev, total));
+  TRY(dalloc(c, w_out, total));
+  CUDA_TRY(c, cudaMemcpy(*ptr_dev, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(*col_dev, col.data(), total * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(*w_out, wt.data(), total * sizeof(float), cudaMemcpyHostToDevice));
+  return SLLBM_OK;
+}
+
+static double lagrange_host(const double* nodes, int P, int a, double r) {
+  double acc = 1.0;
+  for (int b = 0; b <= P; ++b)
+    if (b != a) acc *= (r - nodes[b]) / (nodes[a] - nodes[b]);
+  return acc;
+}
+
+static sllbm_status build_mapped_transpose(sllbm_ctx* c) {
+  const long long nv = c->nv;
+  const int P = c->P, nx = c->nx, ny = c->ny;
+  const size_t n = (size_t)kQ * nv;
+  std::vector<int> cx(n), cy(n);
+  std::vector<double> r(n), s(n);
+  CUDA_TRY(c, cudaMemcpyAsync(cx.data(), c->dcx, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(cy.data(), c->dcy, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(r.data(), c->dr64, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(s.data(), c->ds64, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const int per = (P + 1) * (P + 1);
+  std::vector<long long> ptr((size_t)kQ * (nv + 1), 0);
+  for (int i = 0; i < kQ; ++i) {
+    long long* p0 = &ptr[(size_t)i * (nv + 1)];
+    for (long long v = 0; v < nv; ++v) {
+      const size_t d = (size_t)i * nv + v;
+      for (int kb = 0; kb <= P; ++kb)
+        for (int ka = 0; ka <= P; ++ka) {
+          const int sx = wrap_index(cx[d] * P + ka, nx, c->ax.periodic);
+          const int sy = wrap_index(cy[d] * P + kb, ny, c->ay.periodic);
+          p0[(long long)sy * nx + sx + 1]++;
+        }
+    }
+  }
+  long long total = 0;
+  for (int i = 0; i < kQ; ++i) {
+    long long* p0 = &ptr[(size_t)i * (nv + 1)];
+    p0[0] = total;
+    for (long long v = 0; v < nv; ++v) p0[v + 1] += p0[v];
+    total = p0[nv];
+  }
+  (void)per;
+  std::vector<int> col(total);
+  std::vector<float> wt(total);
+  std::vector<long long> fill(ptr.begin(), ptr.end());
+  for (int i = 0; i < kQ; ++i)
+    for (long long v = 0; v < nv; ++v) {
+      const size_t d = (size_t)i * nv + v;
+      for (int kb = 0; kb <= P; ++kb)
+        for (int ka = 0; ka <= P; ++ka) {
+          const int sx = wrap_index(cx[d] * P + ka, nx, c->ax.periodic);
+          const int sy = wrap_index(cy[d] * P + kb, ny, c->ay.periodic);
+          const long long e = fill[(size_t)i * (nv + 1) + (long long)sy * nx + sx]++;
+          col[e] = (int)v;
+          wt[e] = (float)(lagrange_host(c->ax.nodes, P, ka, r[d]) * lagrange_host(c->ay.nodes, P, kb, s[d]));
+        }
+    }
+  TRY(dalloc(c, &c->tm_ptr, ptr.size()));
+  TRY(dalloc(c, &c->tm_col, (size_t)total));
+  TRY(dalloc(c, &c->tm_w, (size_t)total));
+  CUDA_TRY(c, cudaMemcpy(c->tm_ptr, ptr.data(), ptr.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->tm_col, col.data(), (size_t)total * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->tm_w, wt.data(), (size_t)total * sizeof(float), cudaMemcpyHostToDevice));
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_out, const float* moments) {
+  if (!c || !lam_in || !lam_out || !moments) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  if (lam_in == lam_out) return fail(c, SLLBM_ERR_ARG, "lambda_in and lambda_out alias");
+  if (!c->precomputed) return fail(c, SLLBM_ERR_STATE, "precompute_departures first");
+  const bool mapped = c->map.kind != SLLBM_MAP_IDENTITY;
+  if (!c->transposed) {
+    if (!c->mu) TRY(dalloc(c, &c->mu, (size_t)2 * kQ * c->nv));
+    if (mapped)
+      TRY(build_mapped_transpose(c));
+    else {
+      TRY(build_axis_transpose(c, c->ax, c->offx, c->wx64, &c->tx_ptr, &c->tx_col, &c->tx_w));
+      TRY(build_axis_transpose(c, c->ay, c->offy, c->wy64, &c->ty_ptr, &c->ty_col, &c->ty_w));
+    }
+    c->transposed = true;
+  }
+  AdjointArgs a{};
+  a.lam_in = lam_in;
+  a.lam_out = lam_out;
+  a.mu = c->mu;
+  a.moments = moments;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nv = c->nv;
+  a.cs = c->cs;
+  a.cp = c->cp;
+  a.mapped = mapped;
+  a.tx_ptr = c->tx_ptr;
+  a.tx_col = c->tx_col;
+  a.tx_w = c->tx_w;
+  a.ty_ptr = c->ty_ptr;
+  a.ty_col = c->ty_col;
+  a.ty_w = c->ty_w;
+  a.tm_ptr = c->tm_ptr;
+  a.tm_col = c->tm_col;
+  a.tm_w = c->tm_w;
+  CUDA_TRY(c, launch_adjoint_step(a, c->stream));
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_init_equilibrium_vjp(sllbm_ctx* c, const double* rho, const double* u, const double* v,
+                                        const double* T, const float* lam0, float* du, float* dv) {
+  if (!c || !rho || !u || !v || !T || !lam0 || !du || !dv) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  InitVjpArgs a{};
+  a.rho = rho;
+  a.u = u;
+  a.v = v;
+  a.T = T;
+  a.lam = lam0;
+  a.du = du;
+  a.dv = dv;
+  a.nv = c->nv;
+  a.cs = c->cs;
+  a.cp = c->cp;
+  CUDA_TRY(c, launch_init_vjp(a, c->stream));
+  return SLLBM_OK;
+}
+
+}  // extern "C"

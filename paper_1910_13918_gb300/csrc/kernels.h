@@ -1,0 +1,132 @@
+// Host-side launch interface of the SLLBM kernels (one translation unit per kernel family).
+#pragma once
+
+#include <stddef.h>
+
+#include "sllbm_internal.cuh"
+
+namespace sllbm {
+
+enum StoreKind { kStoreF32 = 0, kStoreBF16 = 1, kStoreF64 = 2 };
+
+// Everything a step kernel needs.  Uniform grids use the per-axis tables (off*, w*), transformed
+// grids (or uniform grids with departure offsets beyond the fused kernel's halo) the per-(velocity,
+// vertex) descriptors (dc*, dr/ds).  Offsets off[c][j] are stencil start minus vertex index.
+struct StepArgs {
+  const void* src;
+  void* dst;
+  int nx, ny, pitch, periodic_x, periodic_y, P;
+  long long nv;
+  size_t plane_stride;  // elements between population planes (ny * pitch)
+  const int* offx;
+  const int* offy;
+  const float* wx;      // [5][nx][P+1]
+  const float* wy;      // [5][ny][P+1]
+  const double* wx64;
+  const double* wy64;
+  const int* dcx;       // [25][nv] departure cell index in x
+  const int* dcy;
+  const float* dr;      // [25][nv] local reference coordinate in the cell
+  const float* ds;
+  const double* dr64;
+  const double* ds64;
+  float nodesf[5];
+  double nodes[5];
+  Consts cs;
+  CollideK cp;
+  int* flag;            // bit 0: unstable
+  int mapped;           // 1: use descriptors
+  // fused uniform kernel geometry
+  int offx_min, offx_max, offy_min, offy_max;
+};
+
+// Generic FP32 gather step (one thread per vertex, (p+1)^2 gathers per plane from L1/L2).
+cudaError_t launch_step_gather(const StepArgs& a, int store, cudaStream_t s);
+// Fused shared-memory step for uniform grids (sum-factorised interpolation); returns
+// cudaErrorNotSupported if the halo does not fit the kernel's staging tile.
+cudaError_t launch_step_uniform(const StepArgs& a, int store, cudaStream_t s);
+bool uniform_kernel_fits(const StepArgs& a);
+// Plain FP64 step on full populations.
+cudaError_t launch_step_plain_f64(const StepArgs& a, cudaStream_t s);
+
+// ---- precompute (FP64) ----
+struct GeomArgs {
+  AxisK ax, ay;
+  MapK map;
+  Consts cs;
+  double dt;
+  int nx, ny;
+  long long nv;
+  int* flag;            // bit 1: Newton failure
+};
+cudaError_t launch_axis_tables(const AxisK& ax, const Consts& cs, double dt, int* off, float* w32,
+                               double* w64, cudaStream_t s);
+cudaError_t launch_descriptors(const GeomArgs& g, int* dcx, int* dcy, float* dr, float* ds,
+                               double* dr64, double* ds64, cudaStream_t s);
+cudaError_t launch_vertex_coords(const GeomArgs& g, double* x, double* y, cudaStream_t s);
+cudaError_t launch_vertex_weights(const GeomArgs& g, const double* gl_x, const double* gl_w,
+                                  int ngl, double* A, cudaStream_t s);
+struct InitArgs {
+  const double *rho, *u, *v, *T;
+  void* dst;
+  int nx, ny, pitch;
+  long long nv;
+  size_t plane_stride;
+  Consts cs;
+  CollideK cp;
+  int store;
+};
+cudaError_t launch_init_equilibrium(const InitArgs& a, cudaStream_t s);
+
+// ---- moments and reductions ----
+struct MomentArgs {
+  const void* src;
+  int nx, ny, pitch;
+  long long nv;
+  size_t plane_stride;
+  Consts cs;
+  CollideK cp;
+  int store;
+  const double* A;
+  float *rho, *u, *v, *T;
+  double* partials;   // [2][nblocks] scratch for the deterministic reduction
+  double* sums;       // [2] device result (may be null when partials is null)
+  int* flag;
+};
+int moments_blocks(long long nv);
+cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s);
+
+// ---- adjoint ----
+struct AdjointArgs {
+  const float* lam_in;
+  float* lam_out;
+  float* mu;           // [2][25][nv] scratch: J_C^T lambda
+  const float* moments;  // [4][nv]
+  int nx, ny;
+  long long nv;
+  Consts cs;
+  CollideK cp;
+  // transposed stencils: uniform per axis (CSR over vertex index per component), mapped per velocity
+  int mapped;
+  const int* tx_ptr;   // [5][nx+1]
+  const int* tx_col;
+  const float* tx_w;
+  const int* ty_ptr;   // [5][ny+1]
+  const int* ty_col;
+  const float* ty_w;
+  const long long* tm_ptr;  // [25][nv+1]
+  const int* tm_col;
+  const float* tm_w;
+};
+cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s);
+struct InitVjpArgs {
+  const double *rho, *u, *v, *T;
+  const float* lam;
+  float *du, *dv;
+  long long nv;
+  Consts cs;
+  CollideK cp;
+};
+cudaError_t launch_init_vjp(const InitVjpArgs& a, cudaStream_t s);
+
+}  // namespace sllbm

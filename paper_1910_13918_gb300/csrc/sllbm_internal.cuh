@@ -1,0 +1,217 @@
+// Internal definitions shared by the kernels and the host library of the SLLBM (arXiv:1910.13918).
+//
+// Conventions: a population plane is [ny][pitch] (x fastest); the state is [npop][25][ny][pitch];
+// velocity i = 5a + b with a (b) the D1Q5 index of the x (y) component (Table I order).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sllbm {
+
+constexpr int kQ1 = 5;   // D1Q5
+constexpr int kQ = 25;   // D2Q25
+
+// Velocity set (Sec. II.B, Table I) and the 1D Hermite table he[k][a] = He_k(xi_a) / k!.
+// The fourth-order equilibrium of Sec. II.A factorises over the two axes:
+//   f_ab^eq = w_a w_b rho sum_{k+l<=4} A_k(u_x) he[k][a] * A_l(u_y) he[l][b]
+// with A_0 = 1, A_1 = u, A_2 = u^2 + q, A_3 = u^3 + 3uq, A_4 = u^4 + 6u^2 q + 3q^2, q = theta - 1
+// (the 1D Hermite moments of a Maxwellian; the tensor coefficients a_eq^(n) of Eq. moments are
+// their products).
+struct Consts {
+  double xi[kQ1], w[kQ1];
+  double he[kQ1][kQ1];
+  float xif[kQ1], wf[kQ1], hef[kQ1][kQ1];
+};
+
+// One axis of the grid as the kernels see it (Sec. II.E): n_cells cells of order p on [lo, hi].
+struct AxisK {
+  int n_cells, p, nv, periodic;
+  double lo, hi, hc, len;
+  double nodes[5];
+};
+
+// Grid transformation (identity or the sine map of sllbm.h).
+struct MapK {
+  int kind;
+  double a;
+};
+
+// BGK parameters (Eq. streaming_fg with Pr = 1).
+struct CollideK {
+  double omega, cv, K;    // 1/tau, C_v, K = 2 C_v - D
+  float omegaf, cvf, Kf;
+  int npop;
+};
+
+// ------------------------------------------------------------------------------------------
+// storage helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float ld_store(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_store(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+__device__ __forceinline__ void st_store(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+__host__ __device__ __forceinline__ int wrap_index(int j, int n, int periodic) {
+  if (!periodic) return j;
+  j %= n;
+  return j < 0 ? j + n : j;
+}
+
+// ------------------------------------------------------------------------------------------
+// geometry helpers (FP64)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double fold_axis(double x, const AxisK& ax) {
+  if (ax.periodic) {
+    double s = fmod(x - ax.lo, ax.len);
+    if (s < 0.0) s += ax.len;
+    return ax.lo + s;
+  }
+  return fmin(fmax(x, ax.lo), ax.hi);
+}
+
+__device__ __forceinline__ void locate_axis(double x, const AxisK& ax, int* cell, double* r) {
+  double s = (x - ax.lo) / ax.hc;
+  int c = (int)floor(s);
+  c = c < 0 ? 0 : (c > ax.n_cells - 1 ? ax.n_cells - 1 : c);
+  *cell = c;
+  *r = s - (double)c;
+}
+
+__device__ __forceinline__ double vertex_ref_coord(int j, const AxisK& ax) {
+  if (!ax.periodic && j == ax.nv - 1) return ax.hi;
+  int c = j / ax.p, k = j % ax.p;
+  return ax.lo + ax.hc * ((double)c + ax.nodes[k]);
+}
+
+// Lagrange basis psi_a(r) on the support points of the reference interval (Eq. sl_streaming).
+template <int P, typename T>
+__device__ __forceinline__ void lagrange_basis(const T* nodes, T r, T* psi) {
+#pragma unroll
+  for (int a = 0; a <= P; ++a) {
+    T acc = T(1);
+#pragma unroll
+    for (int b = 0; b <= P; ++b)
+      if (b != a) acc *= (r - nodes[b]) / (nodes[a] - nodes[b]);
+    psi[a] = acc;
+  }
+}
+
+__device__ __forceinline__ void sine_map(double a, double xi, double eta, double* x, double* y) {
+  const double pi = 3.141592653589793238462643383279502884;
+  *x = xi + a * sin(2.0 * pi * xi) * sin(pi * eta);
+  *y = eta + a * sin(pi * xi) * sin(2.0 * pi * eta);
+}
+
+__device__ __forceinline__ void sine_map_jac(double a, double xi, double eta, double* j11,
+                                             double* j12, double* j21, double* j22) {
+  const double pi = 3.141592653589793238462643383279502884;
+  *j11 = 1.0 + 2.0 * pi * a * cos(2.0 * pi * xi) * sin(pi * eta);
+  *j12 = pi * a * sin(2.0 * pi * xi) * cos(pi * eta);
+  *j21 = pi * a * cos(pi * xi) * sin(2.0 * pi * eta);
+  *j22 = 1.0 + 2.0 * pi * a * sin(pi * xi) * cos(2.0 * pi * eta);
+}
+
+// ------------------------------------------------------------------------------------------
+// equilibrium (closed, factorised form of Sec. II.A) -- templated on the arithmetic type
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct EqFactors {
+  T X[4][kQ1];   // X[k-1][a] = A_k(u_x) he[k][a], k = 1..4
+  T S[5][kQ1];   // S[m][b]   = sum_{l=1..m} A_l(u_y) he[l][b]
+};
+
+template <typename T>
+__device__ __forceinline__ void eq_factors(const T (&he)[kQ1][kQ1], T ux, T uy, T q,
+                                           EqFactors<T>& e) {
+  T ax[5], ay[5];
+  ax[1] = ux;
+  ax[2] = ux * ux + q;
+  ax[3] = ux * (ux * ux + T(3) * q);
+  ax[4] = ux * ux * (ux * ux + T(6) * q) + T(3) * q * q;
+  ay[1] = uy;
+  ay[2] = uy * uy + q;
+  ay[3] = uy * (uy * uy + T(3) * q);
+  ay[4] = uy * uy * (uy * uy + T(6) * q) + T(3) * q * q;
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a) {
+#pragma unroll
+    for (int k = 1; k <= 4; ++k) e.X[k - 1][a] = ax[k] * he[k][a];
+  }
+#pragma unroll
+  for (int b = 0; b < kQ1; ++b) {
+    e.S[0][b] = T(0);
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) e.S[m][b] = e.S[m - 1][b] + ay[m] * he[m][b];
+  }
+}
+
+// E_ab - 1 where f_ab^eq = w_ab rho E_ab; computed without cancellation against 1.
+template <typename T>
+__device__ __forceinline__ T eq_em1(const EqFactors<T>& e, int a, int b) {
+  T s = e.S[4][b];
+#pragma unroll
+  for (int k = 1; k <= 4; ++k) s += e.X[k - 1][a] * (T(1) + e.S[4 - k][b]);
+  return s;
+}
+
+// Collision of one vertex in deviation form, FP32.  vals[0..24] = f - w (pre-collision),
+// vals[25..49] = g - K w.  On return vals hold the post-collision deviations.  Returns false if
+// the density or temperature is non-positive or non-finite.
+__device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], const Consts& cs,
+                                                      const CollideK& cp) {
+  // moments (Sec. II): rho = 1 + sum fbar, j = sum fbar xi, A2 = sum fbar |xi|^2, G = sum gbar
+  float rowsum[kQ1], colsum[kQ1];
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a) rowsum[a] = 0.f;
+#pragma unroll
+  for (int b = 0; b < kQ1; ++b) colsum[b] = 0.f;
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a)
+#pragma unroll
+    for (int b = 0; b < kQ1; ++b) {
+      rowsum[a] += vals[5 * a + b];
+      colsum[b] += vals[5 * a + b];
+    }
+  float drho = 0.f, jx = 0.f, jy = 0.f, a2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a) {
+    drho += rowsum[a];
+    jx += cs.xif[a] * rowsum[a];
+    jy += cs.xif[a] * colsum[a];
+    a2 += cs.xif[a] * cs.xif[a] * (rowsum[a] + colsum[a]);
+  }
+  float G = 0.f;
+  if (cp.npop == 2) {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) G += vals[kQ + i];
+  }
+  const float rho = 1.f + drho;
+  const float inv_rho = 1.f / rho;
+  const float ux = jx * inv_rho, uy = jy * inv_rho;
+  // theta - 1 = (A2 + G - rho |u|^2 - 2 C_v drho) / (2 C_v rho)
+  const float q = (a2 + G - rho * (ux * ux + uy * uy) - 2.f * cp.cvf * drho) * inv_rho /
+                  (2.f * cp.cvf);
+  EqFactors<float> e;
+  eq_factors<float>(cs.hef, ux, uy, q, e);
+  const float om = cp.omegaf, keep = 1.f - cp.omegaf;
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a)
+#pragma unroll
+    for (int b = 0; b < kQ1; ++b) {
+      const int i = 5 * a + b;
+      const float wab = cs.wf[a] * cs.wf[b];
+      const float devf = drho + rho * eq_em1<float>(e, a, b);   // f^eq / w - 1
+      vals[i] = keep * vals[i] + om * wab * devf;
+      if (cp.npop == 2) {
+        const float devg = devf + q * (1.f + devf);                // g^eq / (K w) - 1
+        vals[kQ + i] = keep * vals[kQ + i] + om * cp.Kf * wab * devg;
+      }
+    }
+  return (rho > 0.f) && (q > -1.f) && isfinite(rho) && isfinite(q);
+}
+
+}  // namespace sllbm

@@ -1,0 +1,102 @@
+// Generic fused SLLBM step, FP32 arithmetic: one thread per vertex gathers the (p+1)^2 stencil of
+// every velocity plane straight from global memory (L1/L2 cached), then collides.
+//
+// Used for transformed grids (per-(velocity, vertex) departure descriptors, Sec. III.E) and for
+// uniform grids whose departure offsets exceed the staging halo of the fused uniform kernel.
+// Pull streaming of Eq. sl_streaming with the BGK collision of Eq. streaming_fg (Pr = 1).
+#include "kernels.h"
+
+namespace sllbm {
+
+template <int P, typename Store, bool Mapped>
+__global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant__ StepArgs a) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= a.nv) return;
+  const int ix = (int)(v % a.nx), iy = (int)(v / a.nx);
+  const Store* src = static_cast<const Store*>(a.src);
+  Store* dst = static_cast<Store*>(a.dst);
+  float vals[2 * kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    const int ia = i / 5, ib = i % 5;
+    int sx, sy;
+    float wx[P + 1], wy[P + 1];
+    if (Mapped) {
+      const long long d = (long long)i * a.nv + v;
+      sx = a.dcx[d] * P;
+      sy = a.dcy[d] * P;
+      lagrange_basis<P, float>(a.nodesf, a.dr[d], wx);
+      lagrange_basis<P, float>(a.nodesf, a.ds[d], wy);
+    } else {
+      sx = ix + a.offx[ia * a.nx + ix];
+      sy = iy + a.offy[ib * a.ny + iy];
+#pragma unroll
+      for (int k = 0; k <= P; ++k) {
+        wx[k] = a.wx[(ia * a.nx + ix) * (P + 1) + k];
+        wy[k] = a.wy[(ib * a.ny + iy) * (P + 1) + k];
+      }
+    }
+    int col[P + 1];
+    long long row[P + 1];
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      col[k] = wrap_index(sx + k, a.nx, a.periodic_x);
+      row[k] = (long long)wrap_index(sy + k, a.ny, a.periodic_y) * a.pitch;
+    }
+#pragma unroll
+    for (int pop = 0; pop < 2; ++pop) {
+      if (pop < a.cp.npop) {
+        const Store* pl = src + (size_t)(pop * kQ + i) * a.plane_stride;
+        float acc = 0.f;
+#pragma unroll
+        for (int kb = 0; kb <= P; ++kb) {
+          float accx = 0.f;
+#pragma unroll
+          for (int ka = 0; ka <= P; ++ka) accx += wx[ka] * ld_store(pl + row[kb] + col[ka]);
+          acc += wy[kb] * accx;
+        }
+        vals[pop * kQ + i] = acc;
+      } else {
+        vals[pop * kQ + i] = 0.f;
+      }
+    }
+  }
+  const bool ok = collide_deviation_f32(vals, a.cs, a.cp);
+  if (!ok) atomicOr(a.flag, 1);
+  const size_t o = (size_t)iy * a.pitch + ix;
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) st_store(dst + (size_t)i * a.plane_stride + o, vals[i]);
+  if (a.cp.npop == 2) {
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) st_store(dst + (size_t)(kQ + i) * a.plane_stride + o, vals[kQ + i]);
+  }
+}
+
+template <int P, typename Store>
+static cudaError_t launch_p(const StepArgs& a, cudaStream_t s) {
+  const int threads = 128;
+  const unsigned blocks = (unsigned)((a.nv + threads - 1) / threads);
+  if (a.mapped)
+    step_gather_kernel<P, Store, true><<<blocks, threads, 0, s>>>(a);
+  else
+    step_gather_kernel<P, Store, false><<<blocks, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename Store>
+static cudaError_t launch_store(const StepArgs& a, cudaStream_t s) {
+  switch (a.P) {
+    case 1: return launch_p<1, Store>(a, s);
+    case 2: return launch_p<2, Store>(a, s);
+    case 3: return launch_p<3, Store>(a, s);
+    case 4: return launch_p<4, Store>(a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_step_gather(const StepArgs& a, int store, cudaStream_t s) {
+  if (store == kStoreBF16) return launch_store<__nv_bfloat16>(a, s);
+  return launch_store<float>(a, s);
+}
+
+}  // namespace sllbm
