@@ -85,15 +85,18 @@ class Workload:
             T = T * (1.0 + 1e-4 * rng.standard_normal(T.shape))
         return rho, u, v, T
 
-    def resized(self, nx_cells, ny_cells, steps=None, dt=None):
-        """Same physics on another grid; the time step follows the CFL rule unless given."""
+    def resized(self, nx_cells, ny_cells, steps=None, dt=None, keep_tau=False):
+        """Same physics on another grid; the time step follows the CFL rule unless given.
+
+        The viscosity is kept (tau follows dt) unless ``keep_tau``: the Sod and 2D Riemann cases
+        fix tau itself, as the paper does (Sec. III.C, III.D)."""
         w = dataclasses.replace(self, nx_cells=nx_cells, ny_cells=ny_cells)
         if dt is None:
             dt = cfl_dt(w)
         ratio = dt / self.dt
         nu = (self.tau - 0.5) * self.dt
         w.dt = dt
-        w.tau = nu / dt + 0.5
+        w.tau = self.tau if keep_tau else nu / dt + 0.5
         w.steps = steps if steps is not None else max(1, int(round(self.steps / ratio)))
         return w
 
@@ -132,13 +135,24 @@ RIEMANN_STATES = {  # (rho, u, v, p) per quadrant, interfaces at x = y = 0.8
 }
 
 
+# The 2D Riemann states of the paper's Table III (Lax-Liu), quadrants split at x = y = 0.5.
+RIEMANN_STATES_PAPER = {
+    "NW": (1.0, 0.7276, 0.0, 1.0),
+    "NE": (0.5313, 0.0, 0.0, 0.4),
+    "SW": (0.8, 0.0, 0.0, 1.0),
+    "SE": (1.0, 0.0, 0.7276, 1.0),
+}
+
+
 def _riemann(w, x, y):
-    east = x >= 0.8
-    north = y >= 0.8
+    states = w.extra.get("states", RIEMANN_STATES)
+    split = w.extra.get("split", 0.8)
+    east = x >= split
+    north = y >= split
     out = [np.zeros_like(x) for _ in range(4)]
     for key, mask in (("NE", east & north), ("NW", ~east & north),
                       ("SW", ~east & ~north), ("SE", east & ~north)):
-        st = RIEMANN_STATES[key]
+        st = states[key]
         for k in range(4):
             out[k] = np.where(mask, st[k], out[k])
     rho, u, v, p = out
@@ -243,6 +257,16 @@ def riemann():
     return w
 
 
+def riemann_paper():
+    """The same 1024x1024-cell p = 3 grid with the milder quadrant states of Table III."""
+    w = riemann()
+    w.name = "riemann1024_p3_tableIII"
+    w.kind = "riemann"
+    w.extra = {"states": RIEMANN_STATES_PAPER, "split": 0.5}
+    w.seed = 6
+    return w
+
+
 def svi():
     """Shock-vortex interaction on the sine-mapped grid [0,2]x[0,1], 512x256 cells, p = 2."""
     radius = 0.075
@@ -254,4 +278,5 @@ def svi():
                            "x_shock": 0.5, "x_objective": 1.5, "checkpoint_every": 20})
 
 
-ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann, "svi": svi}
+ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
+       "riemann_paper": riemann_paper, "svi": svi}

@@ -17,12 +17,17 @@ def oracle_grid(w: W.Workload):
     return o.Grid(ax, ay, o.SineMap(w.map_a) if w.map_a else None)
 
 
-def oracle_run(w: W.Workload, nsteps, perturb=True):
-    """(rho, u, v, theta) of the oracle after nsteps, each (ny, nx) float64."""
+def oracle_state(w: W.Workload, nsteps, perturb=True):
+    """Oracle post-collision populations (f, g) after nsteps, each (25, ny, nx) float64."""
     grid = oracle_grid(w)
     X, Y = grid.coords()
     f, g = o.initial_state(*w.fields(X, Y, perturb=perturb), w.cv)
-    f, g = o.run(f, g, o.Departures(grid, w.dt), w.tau, w.cv, nsteps)
+    return o.run(f, g, o.Departures(grid, w.dt), w.tau, w.cv, nsteps)
+
+
+def oracle_run(w: W.Workload, nsteps, perturb=True):
+    """(rho, u, v, theta) of the oracle after nsteps, each (ny, nx) float64."""
+    f, g = oracle_state(w, nsteps, perturb)
     rho, u, th = o.macroscopic(f, g, w.cv)
     return rho, u[..., 0], u[..., 1], th
 
@@ -94,13 +99,13 @@ def small_workloads():
         "tgv16": W.tgv16(),
         "tgv256": W.tgv256().resized(9, 7, steps=100),
         "sod": _sod_small(),
-        "riemann": W.riemann().resized(20, 21, steps=100),
+        "riemann": W.riemann_paper().resized(20, 21, steps=100, keep_tau=True),
         "svi": _svi_small(),
     }
 
 
 def _sod_small():
-    w = W.sod().resized(64, 2, steps=100)
+    w = W.sod().resized(64, 2, steps=100, keep_tau=True)
     w.y1 = w.y0 + (w.x1 - w.x0) / 64 * 2
     return w
 
