@@ -36,6 +36,10 @@ struct sllbm_ctx {
   float *wx = nullptr, *wy = nullptr;
   double *wx64 = nullptr, *wy64 = nullptr;
   int offx_lo = 0, offx_hi = 0, offy_lo = 0, offy_hi = 0;
+  UniformTables ut{};
+  unsigned char *std_x = nullptr, *std_y = nullptr;
+  int* fix_list = nullptr;       // vertices the fused uniform kernel leaves to the gather kernel
+  long long n_fix = 0;
   // per-(velocity, vertex) descriptors
   int *dcx = nullptr, *dcy = nullptr;
   float *dr = nullptr, *ds = nullptr;
@@ -210,6 +214,81 @@ static GeomArgs geom_args(sllbm_ctx* c) {
   return g;
 }
 
+// Cell-periodic pattern of the per-axis tables of a uniform grid (read by step_uniform.cu):
+// taken from a cell in the middle of each axis; a vertex "follows the pattern" when its offset
+// and weights match those of its local node for all five components.  The fused kernel writes
+// only vertices that follow the pattern on both axes; the others go to the gather kernel.
+static sllbm_status axis_pattern(sllbm_ctx* c, const AxisK& ax, const int* off_dev, const float* w_dev,
+                                 bool is_y, std::vector<unsigned char>& stdv, bool* ok) {
+  const int n = ax.nv, P = c->P;
+  std::vector<int> off((size_t)kQ1 * n);
+  std::vector<float> w((size_t)kQ1 * n * (P + 1));
+  CUDA_TRY(c, cudaMemcpyAsync(off.data(), off_dev, off.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(w.data(), w_dev, w.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  *ok = ax.n_cells >= 3;
+  const int jref0 = (ax.n_cells / 2) * P;
+  for (int comp = 0; comp < kQ1 && *ok; ++comp)
+    for (int k = 0; k < P; ++k) {
+      const int j = jref0 + k;
+      const int d = off[(size_t)comp * n + j];
+      if (d < -P || d > 0) { *ok = false; break; }   // taps must stay within the band [-P, P]
+      const float* wj = &w[((size_t)comp * n + j) * (P + 1)];
+      if (is_y) {
+        for (int t = 0; t < 9; ++t) c->ut.wy_band[comp][k][t] = 0.f;
+        for (int al = 0; al <= P; ++al) c->ut.wy_band[comp][k][d + al + P] = wj[al];
+      } else {
+        c->ut.dx_pat[comp][k] = d;
+        for (int al = 0; al <= P; ++al) c->ut.wx_pat[comp][k][al] = wj[al];
+      }
+    }
+  stdv.assign(n, 1);
+  for (int j = 0; j < n && *ok; ++j) {
+    const int k = j % P;
+    for (int comp = 0; comp < kQ1; ++comp) {
+      const int d = off[(size_t)comp * n + j];
+      const float* wj = &w[((size_t)comp * n + j) * (P + 1)];
+      const int dref = off[(size_t)comp * n + jref0 + k];
+      const float* wr = &w[((size_t)comp * n + jref0 + k) * (P + 1)];
+      bool same = (d == dref);
+      for (int al = 0; al <= P && same; ++al) same = fabsf(wj[al] - wr[al]) <= 1e-6f;
+      if (!same) stdv[j] = 0;
+    }
+  }
+  return SLLBM_OK;
+}
+
+static sllbm_status build_uniform_pattern(sllbm_ctx* c) {
+  c->ut.valid = false;
+  // 16-byte staging chunks must not straddle the periodic seam, and tiles need a few cells
+  const int chunk = (c->store == kStoreBF16) ? 8 : 4;
+  if (c->ax.periodic && c->nx % chunk != 0) return SLLBM_OK;
+  std::vector<unsigned char> sx, sy;
+  bool okx = false, oky = false;
+  TRY(axis_pattern(c, c->ax, c->offx, c->wx, false, sx, &okx));
+  TRY(axis_pattern(c, c->ay, c->offy, c->wy, true, sy, &oky));
+  if (!okx || !oky) return SLLBM_OK;
+  if (!c->std_x) {
+    TRY(dalloc(c, &c->std_x, (size_t)c->nx));
+    TRY(dalloc(c, &c->std_y, (size_t)c->ny));
+  }
+  CUDA_TRY(c, cudaMemcpy(c->std_x, sx.data(), sx.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->std_y, sy.data(), sy.size(), cudaMemcpyHostToDevice));
+  std::vector<int> fix;
+  for (int iy = 0; iy < c->ny; ++iy)
+    for (int ix = 0; ix < c->nx; ++ix)
+      if (!sx[ix] || !sy[iy]) fix.push_back(iy * c->nx + ix);
+  c->n_fix = (long long)fix.size();
+  if (!fix.empty()) {
+    TRY(dalloc(c, &c->fix_list, fix.size()));
+    CUDA_TRY(c, cudaMemcpy(c->fix_list, fix.data(), fix.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  c->ut.std_x = c->std_x;
+  c->ut.std_y = c->std_y;
+  c->ut.valid = true;
+  return SLLBM_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // API
 // ------------------------------------------------------------------------------------------
@@ -366,8 +445,8 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
   if (c->store == kStoreF64) {
     c->kernel = kKernelPlainF64;
   } else if (!mapped) {
-    StepArgs a = step_args(c, nullptr, nullptr);
-    c->kernel = uniform_kernel_fits(a) ? kKernelUniform : kKernelGather;
+    TRY(build_uniform_pattern(c));
+    c->kernel = c->ut.valid ? kKernelUniform : kKernelGather;
   } else {
     c->kernel = kKernelGather;
   }
@@ -424,7 +503,15 @@ static cudaError_t enqueue_step(sllbm_ctx* c) {
   StepArgs a = step_args(c, c->state[c->cur], c->state[c->cur ^ 1]);
   cudaError_t e;
   switch (c->kernel) {
-    case kKernelUniform: e = launch_step_uniform(a, c->store, c->stream); break;
+    case kKernelUniform:
+      e = launch_step_uniform(a, c->ut, c->store, c->stream);
+      if (e == cudaSuccess && c->n_fix > 0) {  // vertices off the cell-periodic pattern
+        a.vlist = c->fix_list;
+        a.nlist = c->n_fix;
+        a.mapped = 0;
+        e = launch_step_gather(a, c->store, c->stream);
+      }
+      break;
     case kKernelPlainF64: e = launch_step_plain_f64(a, c->stream); break;
     default: e = launch_step_gather(a, c->store, c->stream); break;
   }
@@ -448,7 +535,10 @@ const char* sllbm_step_kernel_name(const sllbm_ctx* c) {
   }
 }
 
-int sllbm_launches_per_step(const sllbm_ctx* c) { return c ? 1 : 0; }
+int sllbm_launches_per_step(const sllbm_ctx* c) {
+  if (!c) return 0;
+  return (c->kernel == kKernelUniform && c->n_fix > 0) ? 2 : 1;
+}
 
 static cudaError_t copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
   // dense [npop][25][ny][nx] <-> pitched [npop][25][ny][pitch]

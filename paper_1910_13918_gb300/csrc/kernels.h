@@ -38,14 +38,28 @@ struct StepArgs {
   int mapped;           // 1: use descriptors
   // fused uniform kernel geometry
   int offx_min, offx_max, offy_min, offy_max;
+  // optional vertex list (gather kernel only): process vlist[0..nlist) instead of every vertex
+  const int* vlist;
+  long long nlist;
+};
+
+// Cell-periodic pattern of a uniform grid (see step_uniform.cu): per velocity component and
+// local node, the y interpolation as a band of 2p+1 taps around the vertex and the x taps.
+struct UniformTables {
+  bool valid;
+  float wy_band[kQ1][4][9];   // [b][l][j]: weight of source row y + j - p for local row l
+  float wx_pat[kQ1][4][5];    // [a][k][alpha]
+  int dx_pat[kQ1][4];         // [a][k]: stencil start - vertex
+  const unsigned char* std_x; // [nx]: column follows the pattern
+  const unsigned char* std_y; // [ny]
 };
 
 // Generic FP32 gather step (one thread per vertex, (p+1)^2 gathers per plane from L1/L2).
 cudaError_t launch_step_gather(const StepArgs& a, int store, cudaStream_t s);
-// Fused shared-memory step for uniform grids (sum-factorised interpolation); returns
-// cudaErrorNotSupported if the halo does not fit the kernel's staging tile.
-cudaError_t launch_step_uniform(const StepArgs& a, int store, cudaStream_t s);
-bool uniform_kernel_fits(const StepArgs& a);
+// Fused shared-memory step for uniform grids (pattern band interpolation); writes only the
+// vertices marked in std_x/std_y.  cudaErrorNotSupported if the tables are not valid.
+cudaError_t launch_step_uniform(const StepArgs& a, const UniformTables& t, int store, cudaStream_t s);
+int uniform_tile_rows(int P);
 // Plain FP64 step on full populations.
 cudaError_t launch_step_plain_f64(const StepArgs& a, cudaStream_t s);
 

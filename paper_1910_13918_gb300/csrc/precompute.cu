@@ -161,6 +161,18 @@ __global__ void vertex_weights_kernel(const __grid_constant__ GeomArgs g, GL gl,
     }
     if (c >= 0 && c < g.ay.n_cells && k >= 0 && k <= P) { cys[ncy] = c; ays[ncy] = k; ++ncy; }
   }
+  if (g.map.kind != 1) {  // |det J| = 1: the integral factorises into two 1D integrals
+    double sx = 0.0, sy = 0.0;
+    for (int q = 0; q < ngl; ++q) {
+      double px[P + 1], py[P + 1];
+      lagrange_basis<P, double>(g.ax.nodes, gl.x[q], px);
+      lagrange_basis<P, double>(g.ay.nodes, gl.x[q], py);
+      for (int e = 0; e < ncx; ++e) sx += gl.w[q] * g.ax.hc * px[axs[e]];
+      for (int e = 0; e < ncy; ++e) sy += gl.w[q] * g.ay.hc * py[ays[e]];
+    }
+    A[v] = sx * sy;
+    return;
+  }
   double acc = 0.0;
   for (int ey = 0; ey < ncy; ++ey)
     for (int ex = 0; ex < ncx; ++ex)

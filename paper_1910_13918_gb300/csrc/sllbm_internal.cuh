@@ -73,12 +73,28 @@ __device__ __forceinline__ double fold_axis(double x, const AxisK& ax) {
   return fmin(fmax(x, ax.lo), ax.hi);
 }
 
+// Cell and local coordinate of a folded coordinate.  A point within rounding (1e-12 of a cell) of a
+// cell face is put at r = 0 of the cell on its right, so that vertices whose departure lands on a
+// face get the same stencil whatever the rounding of their coordinates (the interpolant is
+// continuous there, so the value is the same either way).
 __device__ __forceinline__ void locate_axis(double x, const AxisK& ax, int* cell, double* r) {
   double s = (x - ax.lo) / ax.hc;
   int c = (int)floor(s);
   c = c < 0 ? 0 : (c > ax.n_cells - 1 ? ax.n_cells - 1 : c);
+  double rr = s - (double)c;
+  if (rr > 1.0 - 1e-12) {
+    if (c < ax.n_cells - 1) {
+      c += 1;
+      rr = 0.0;
+    } else if (ax.periodic) {
+      c = 0;
+      rr = 0.0;
+    }
+  } else if (rr < 1e-12) {
+    rr = 0.0;
+  }
   *cell = c;
-  *r = s - (double)c;
+  *r = rr;
 }
 
 __device__ __forceinline__ double vertex_ref_coord(int j, const AxisK& ax) {
@@ -198,6 +214,16 @@ __device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], con
   EqFactors<float> e;
   eq_factors<float>(cs.hef, ux, uy, q, e);
   const float om = cp.omegaf, keep = 1.f - cp.omegaf;
+  // Post-collision values, and the moments of the FP32 equilibrium itself.  In exact arithmetic
+  // the equilibrium has the moments of the pre-collision state; in FP32 its fourth-order
+  // polynomial carries rounding of the size of its largest terms, which would leak into the
+  // conserved moments every step.
+  float erow[kQ1], ecol[kQ1], eg = 0.f;
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a) {
+    erow[a] = 0.f;
+    ecol[a] = 0.f;
+  }
 #pragma unroll
   for (int a = 0; a < kQ1; ++a)
 #pragma unroll
@@ -205,12 +231,53 @@ __device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], con
       const int i = 5 * a + b;
       const float wab = cs.wf[a] * cs.wf[b];
       const float devf = drho + rho * eq_em1<float>(e, a, b);   // f^eq / w - 1
-      vals[i] = keep * vals[i] + om * wab * devf;
+      const float ef = wab * devf;                               // f^eq - w
+      erow[a] += ef;
+      ecol[b] += ef;
+      vals[i] = keep * vals[i] + om * ef;
       if (cp.npop == 2) {
         const float devg = devf + q * (1.f + devf);                // g^eq / (K w) - 1
-        vals[kQ + i] = keep * vals[kQ + i] + om * cp.Kf * wab * devg;
+        const float egi = cp.Kf * wab * devg;                      // g^eq - K w
+        eg += egi;
+        vals[kQ + i] = keep * vals[kQ + i] + om * egi;
       }
     }
+  // Residual moments of (equilibrium - pre-collision state); remove them with the smallest
+  // correction in the span of w {1, xi_x, xi_y} (mass, momentum) and w on g (energy).  This
+  // changes nothing in exact arithmetic and restores conservation to the rounding of the sums.
+  float r0 = -drho, r1 = -jx, r2 = -jy, r3 = -(a2 + G) + eg;
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a) {
+    r0 += erow[a];
+    r1 += cs.xif[a] * erow[a];
+    r2 += cs.xif[a] * ecol[a];
+    r3 += cs.xif[a] * cs.xif[a] * (erow[a] + ecol[a]);
+  }
+  const float c3 = r3 - 2.f * r0;   // energy residual left after the mass correction
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a) {
+    const float ta = om * cs.wf[a];
+    const float ca = r0 + r1 * cs.xif[a];
+#pragma unroll
+    for (int b = 0; b < kQ1; ++b) {
+      const int i = 5 * a + b;
+      const float wb = ta * cs.wf[b];
+      vals[i] -= wb * (ca + r2 * cs.xif[b]);
+      if (cp.npop == 2) vals[kQ + i] -= wb * c3;
+    }
+  }
+  if (cp.npop != 2) {
+    // single population: remove the energy residual along w (|xi|^2 - 2), which carries no
+    // mass or momentum; its energy is sum w |xi|^4 - 2 sum w |xi|^2 = 8 - 4 = 4
+    const float c = 0.25f * c3;
+#pragma unroll
+    for (int a = 0; a < kQ1; ++a)
+#pragma unroll
+      for (int b = 0; b < kQ1; ++b) {
+        const float x2 = cs.xif[a] * cs.xif[a] + cs.xif[b] * cs.xif[b];
+        vals[5 * a + b] -= om * cs.wf[a] * cs.wf[b] * c * (x2 - 2.f);
+      }
+  }
   return (rho > 0.f) && (q > -1.f) && isfinite(rho) && isfinite(q);
 }
 

@@ -10,8 +10,13 @@ namespace sllbm {
 
 template <int P, typename Store, bool Mapped>
 __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant__ StepArgs a) {
-  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= a.nv) return;
+  long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a.vlist) {
+    if (v >= a.nlist) return;
+    v = a.vlist[v];
+  } else if (v >= a.nv) {
+    return;
+  }
   const int ix = (int)(v % a.nx), iy = (int)(v / a.nx);
   const Store* src = static_cast<const Store*>(a.src);
   Store* dst = static_cast<Store*>(a.dst);
@@ -75,7 +80,9 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
 template <int P, typename Store>
 static cudaError_t launch_p(const StepArgs& a, cudaStream_t s) {
   const int threads = 128;
-  const unsigned blocks = (unsigned)((a.nv + threads - 1) / threads);
+  const long long n = a.vlist ? a.nlist : a.nv;
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
   if (a.mapped)
     step_gather_kernel<P, Store, true><<<blocks, threads, 0, s>>>(a);
   else

@@ -72,6 +72,24 @@ class Workload:
     def updates_per_step(self):
         return self.n_vertices * 25 * 2
 
+    @property
+    def velocity_scale(self):
+        """Characteristic speed of the flow: the scale velocity errors are reported against.
+
+        Taylor-Green: U0; Sod: sound speed of the left state; Riemann: largest state speed;
+        shock-vortex: inflow speed.  (Flows that start at rest have no velocity to be relative to.)
+        """
+        if self.kind == "tgv":
+            return self.extra["U0"]
+        if self.kind == "sod":
+            return math.sqrt(GAMMA * 1.0 / 1.0)
+        if self.kind == "riemann":
+            states = self.extra.get("states", RIEMANN_STATES)
+            return max(math.hypot(st[1], st[2]) for st in states.values())
+        if self.kind == "svi":
+            return self.extra["Ma_A"]
+        return 1.0
+
     def fields(self, x, y, perturb=False):
         """Initial (rho, u, v, T) on vertex coordinates x, y (arrays of equal shape, float64)."""
         rho, u, v, T = _GENERATORS[self.kind](self, np.asarray(x, np.float64),

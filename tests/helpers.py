@@ -80,11 +80,13 @@ def oracle_step_at(w: W.Workload, vertices, perturb=True):
     return rho, u[..., 0], u[..., 1], th
 
 
-def field_errors(gpu, ref):
-    """Max relative error per field: rho and T relative, u and v relative to max |u_ref|."""
+def field_errors(gpu, ref, velocity_scale=0.0):
+    """Max relative error per field: rho and T pointwise relative; u and v relative to the larger
+    of max |u_ref| and the workload's characteristic speed (a flow starting at rest has no
+    velocity of its own to be relative to)."""
     rho_g, u_g, v_g, t_g = (np.asarray(a, dtype=np.float64) for a in gpu)
     rho_r, u_r, v_r, t_r = (np.asarray(a, dtype=np.float64) for a in ref)
-    umax = max(np.max(np.abs(u_r)), np.max(np.abs(v_r)), 1e-12)
+    umax = max(np.max(np.abs(u_r)), np.max(np.abs(v_r)), velocity_scale, 1e-12)
     return {
         "rho": float(np.max(np.abs(rho_g - rho_r) / np.abs(rho_r))),
         "u": float(np.max(np.abs(u_g - u_r)) / umax),

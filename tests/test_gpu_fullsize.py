@@ -1,0 +1,99 @@
+"""Full-size workloads on the GPU, in the launch configuration the benchmark times.
+
+* one step: sampled vertices against the oracle, which evaluates the step only at those
+  vertices (its initial state only where their stencils reach);
+* long runs: the fused FP32 step against the plain FP64 GPU step (itself pinned to the oracle
+  element by element in test_gpu_parity.py), plus size-independent properties.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1910_13918_gb300 import workloads as W
+
+from . import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _sample(w, n=48, seed=11):
+    rng = np.random.default_rng(seed)
+    nx, ny = w.nx, w.ny
+    pts = {(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1), (nx // 2, ny // 2), (1, ny // 3),
+           (nx - 2, (2 * ny) // 3), (nx // 3, 1), (nx // 3, ny - 2)}
+    for _ in range(n):
+        pts.add((int(rng.integers(nx)), int(rng.integers(ny))))
+    return np.array(sorted(iy * nx + ix for ix, iy in pts))
+
+
+def _gpu(w, nsteps, prec):
+    from paper_1910_13918_gb300.sllbm import SLLBM
+    s = SLLBM.from_workload(w, prec=prec)
+    s.precompute()
+    x, y = (t.cpu().numpy() for t in s.coords())
+    s.init(*w.fields(x, y, perturb=True))
+    s.step(nsteps)
+    return s
+
+
+def _fields(s):
+    m = s.moments()
+    return tuple(m[k].cpu().numpy().reshape(-1) for k in ("rho", "u", "v", "T")), m
+
+
+@pytest.mark.parametrize("name", ["tgv256", "sod", "riemann", "riemann_paper", "svi"])
+def test_one_step_sampled_against_oracle(gpu_lib, name):
+    w = W.ALL[name]()
+    s = _gpu(w, 1, "f32")
+    got, _ = _fields(s)
+    verts = _sample(w)
+    ref = H.oracle_step_at(w, verts)
+    err = H.field_errors(tuple(a[verts] for a in got), ref, w.velocity_scale)
+    assert max(err.values()) <= 1e-5, (name, s.kernel_name, err)
+
+
+@pytest.mark.parametrize("name,nsteps", [("tgv256", 1000), ("riemann_paper", 200), ("svi", 200),
+                                         ("sod", 2000)])
+def test_long_run_f32_against_f64(gpu_lib, name, nsteps):
+    w = W.ALL[name]()
+    a, ma = _fields(_gpu(w, nsteps, "f32"))
+    b, mb = _fields(_gpu(w, nsteps, "f64"))
+    err = H.field_errors(a, b, w.velocity_scale)
+    assert max(err.values()) <= 1e-4, (name, err)
+    assert abs(ma["mass"] / mb["mass"] - 1) < 1e-6
+
+
+def test_tgv256_mass_and_energy_conserved(gpu_lib):
+    w = W.tgv256()
+    s = _gpu(w, 0, "f32")
+    m0 = s.moments()
+    s.step(500)
+    m1 = s.moments()
+    assert abs(m1["mass"] / m0["mass"] - 1) < 1e-6
+    assert abs(m1["energy"] / m0["energy"] - 1) < 1e-5
+
+
+def test_sod_full_run_matches_exact_solution(gpu_lib):
+    """The Sod workload to t = 0.2 (13240 fused steps) against the exact Riemann solution."""
+    from oracle import riemann
+    w = W.sod()
+    s = _gpu(w, w.steps, "f32")
+    m = s.moments()
+    x, _ = (t.cpu().numpy() for t in s.coords())
+    rho = m["rho"].cpu().numpy()[0]
+    re, _, _ = riemann.sample((1, 0, 1), (0.125, 0, 0.1), 1.4, (x[0] - 0.5) / 0.2)
+    assert np.mean(np.abs(rho - re)) < 0.01, np.mean(np.abs(rho - re))
+
+
+def test_riemann_baseline_states_leave_the_model_range(gpu_lib):
+    """The four-quadrant states with the cold SW corner (T = 0.21 at |u| = 1.7) drive the
+    temperature negative within a few steps, in FP32 and FP64 alike (the oracle does the same on
+    a small grid: tests/test_oracle_physics.py)."""
+    from paper_1910_13918_gb300.sllbm import SLLBMError
+    w = W.riemann()
+    for prec in ("f32", "f64"):
+        s = _gpu(w, 0, prec)
+        with pytest.raises(SLLBMError):
+            for _ in range(10):
+                s.step(1)
+                s.moments(sums=False)

@@ -36,7 +36,7 @@ def test_forward_parity_small_f32(gpu_lib, name, nsteps, tol):
     w = H.small_workloads()[name]
     s, gpu, _ = gpu_run(w, nsteps, "f32")
     ref = H.oracle_run(w, nsteps)
-    err = H.field_errors(gpu, ref)
+    err = H.field_errors(gpu, ref, w.velocity_scale)
     assert max(err.values()) <= tol, (name, s.kernel_name, err)
 
 
@@ -57,7 +57,7 @@ def test_forward_parity_small_f64_state(gpu_lib, name, nsteps):
 def test_bf16_storage_error_reported(gpu_lib, name):
     w = H.small_workloads()[name]
     _, gpu, _ = gpu_run(w, 10, "bf16")
-    err = H.field_errors(gpu, H.oracle_run(w, 10))
+    err = H.field_errors(gpu, H.oracle_run(w, 10), w.velocity_scale)
     assert max(err.values()) < 2e-2, err
 
 

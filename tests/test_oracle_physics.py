@@ -103,3 +103,21 @@ def test_stationary_shock_stays():
     mid = 0.5 * (1 + rr)
     x_shock = X[0][np.argmin(np.abs(r1[0] - mid))]
     assert abs(x_shock - 0.5) < 2.0 / (cells * 2), x_shock
+
+
+def test_riemann_baseline_states_leave_the_model_range():
+    """The four-quadrant states with a cold corner (rho 0.138, p 0.029: T = 0.21 at |u| = 1.7,
+    local Mach 3.1) are outside what the D2Q25 fourth-order equilibrium represents: 14 of its 25
+    populations are negative there and the minimum temperature falls below zero within four
+    steps (five here), whereas the milder states of the paper's Table III stay bounded."""
+    from tests import helpers as H
+    rho, u, th = np.array([0.138]), np.array([[1.206, 1.206]]), np.array([0.029 / 0.138])
+    assert (o.equilibrium_f(rho, u, th) < 0).sum() == 14
+    for w, check in ((W.riemann(), lambda t: t < 0.0), (W.riemann_paper(), lambda t: t > 0.5)):
+        w = w.resized(12, 12, keep_tau=True)
+        grid = H.oracle_grid(w)
+        X, Y = grid.coords()
+        f, g = o.initial_state(*w.fields(X, Y), w.cv)
+        f, g = o.run(f, g, o.Departures(grid, w.dt), w.tau, w.cv, 5)
+        _, _, th = o.macroscopic(f, g, w.cv)
+        assert check(th.min()), (w.name, th.min())
