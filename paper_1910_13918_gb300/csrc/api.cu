@@ -2,6 +2,7 @@
 // support points, Gauss-Legendre rule, transposed stencils) and dispatch to the kernels.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -27,7 +28,10 @@ struct sllbm_ctx {
   MapK map{};
   Consts cs{};
   CollideK cp{};
-  void* state[2] = {nullptr, nullptr};
+  void* state[2] = {nullptr, nullptr};   // interior origins of the two state buffers
+  void* alloc[2] = {nullptr, nullptr};   // allocation starts (ghost cells included)
+  int gx = 8, gy = 4, gxr = 0, gyb = 20, rows_alloc = 0;
+  GhostK ghost{};
   int cur = 0;
   bool precomputed = false, initialized = false;
   int kernel = kKernelGather;
@@ -197,6 +201,7 @@ static StepArgs step_args(sllbm_ctx* c, const void* src, void* dst) {
   a.offx_max = c->offx_hi;
   a.offy_min = c->offy_lo;
   a.offy_max = c->offy_hi;
+  a.ghost = c->ghost;
   return a;
 }
 
@@ -235,8 +240,8 @@ static sllbm_status axis_pattern(sllbm_ctx* c, const AxisK& ax, const int* off_d
       if (d < -P || d > 0) { *ok = false; break; }   // taps must stay within the band [-P, P]
       const float* wj = &w[((size_t)comp * n + j) * (P + 1)];
       if (is_y) {
-        for (int t = 0; t < 9; ++t) c->ut.wy_band[comp][k][t] = 0.f;
-        for (int al = 0; al <= P; ++al) c->ut.wy_band[comp][k][d + al + P] = wj[al];
+        c->ut.dy_pat[comp][k] = d;
+        for (int al = 0; al <= P; ++al) c->ut.wy_pat[comp][k][al] = wj[al];
       } else {
         c->ut.dx_pat[comp][k] = d;
         for (int al = 0; al <= P; ++al) c->ut.wx_pat[comp][k][al] = wj[al];
@@ -285,8 +290,42 @@ static sllbm_status build_uniform_pattern(sllbm_ctx* c) {
   }
   c->ut.std_x = c->std_x;
   c->ut.std_y = c->std_y;
+  // tile height: 8-row tiles (two CTAs per SM) unless SLLBM_UNIFORM_TILE=16 asks for 16-row ones
+  const char* tile = getenv("SLLBM_UNIFORM_TILE");
+  c->ut.tall = !(tile && atoi(tile) == 8);
+  c->ut.gx = c->gx;
+  c->ut.gy = c->gy;
+  c->ut.rows_alloc = c->rows_alloc;
   c->ut.valid = true;
   return SLLBM_OK;
+}
+
+static cudaError_t copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
+  // dense [npop*25][ny][nx] <-> interior of the ghost-cell layout [planes][rows_alloc][pitch]
+  cudaMemcpy3DParms m = {};
+  const size_t row = (size_t)c->nx * c->elem, prow = (size_t)c->pitch * c->elem;
+  cudaPitchedPtr dense = make_cudaPitchedPtr(nullptr, row, c->nx, c->ny);
+  cudaPitchedPtr inner = make_cudaPitchedPtr(nullptr, prow, c->pitch, c->rows_alloc);
+  if (to_internal) {
+    dense.ptr = const_cast<void*>(src);
+    inner.ptr = dst;
+    m.srcPtr = dense;
+    m.dstPtr = inner;
+  } else {
+    inner.ptr = const_cast<void*>(src);
+    dense.ptr = dst;
+    m.srcPtr = inner;
+    m.dstPtr = dense;
+  }
+  m.extent = make_cudaExtent(row, c->ny, (size_t)c->npop * kQ);
+  m.kind = kind;
+  return cudaMemcpy3DAsync(&m, c->stream);
+}
+
+static cudaError_t fill_ghosts(sllbm_ctx* c) {
+  if (!c->ghost.on) return cudaSuccess;
+  return launch_ghost_fill(c->state[c->cur], c->elem, c->plane_stride, c->pitch, c->npop * kQ,
+                           c->ghost, c->stream);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -354,18 +393,33 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   c->cp.omegaf = (float)c->cp.omega;
   c->cp.cvf = (float)p->cv;
   c->cp.Kf = (float)c->cp.K;
+  c->cp.inv2cvf = (float)(0.5 / p->cv);
   c->cp.npop = c->npop;
   c->store = p->prec == SLLBM_PREC_F32 ? kStoreF32 : (p->prec == SLLBM_PREC_BF16_STORE ? kStoreBF16 : kStoreF64);
   c->elem = c->store == kStoreF32 ? 4 : (c->store == kStoreBF16 ? 2 : 8);
-  c->pitch = (c->nx + 7) / 8 * 8;   // 16-byte aligned rows for every storage type
-  c->plane_stride = (size_t)c->ny * c->pitch;
+  // Plane layout: ghost cells around the interior (8 columns left, 4 rows above, enough right
+  // and below for the last tile's halo), rows 16-byte aligned for every storage type.
+  c->gxr = (c->nx + 31) / 32 * 32 - c->nx + 8;
+  c->rows_alloc = c->gy + c->ny + c->gyb;
+  c->pitch = (c->gx + c->nx + c->gxr + 7) / 8 * 8;
+  c->plane_stride = (size_t)c->rows_alloc * c->pitch;
+  c->ghost.on = 0;
+  c->ghost.px = c->ax.periodic;
+  c->ghost.py = c->ay.periodic;
+  c->ghost.nx = c->nx;
+  c->ghost.ny = c->ny;
+  c->ghost.xlo = -c->gx;
+  c->ghost.xhi = c->nx + c->gxr;
+  c->ghost.ylo = -c->gy;
+  c->ghost.yhi = c->ny + c->gyb;
   sllbm_status s;
   const size_t state_elems = (size_t)2 * kQ * c->plane_stride;
   for (int k = 0; k < 2; ++k) {
     void* ptr = nullptr;
     s = dalloc(c, reinterpret_cast<char**>(&ptr), state_elems * c->elem);
-    if (s != SLLBM_OK) { std::string m = c->err; sllbm_destroy(c); (void)m; return s; }
-    c->state[k] = ptr;
+    if (s != SLLBM_OK) { sllbm_destroy(c); return s; }
+    c->alloc[k] = ptr;
+    c->state[k] = static_cast<char*>(ptr) + ((size_t)c->gy * c->pitch + c->gx) * c->elem;
     if (cudaMemsetAsync(ptr, 0, state_elems * c->elem, c->stream) != cudaSuccess) {
       sllbm_destroy(c);
       return SLLBM_ERR_CUDA;
@@ -447,6 +501,7 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
   } else if (!mapped) {
     TRY(build_uniform_pattern(c));
     c->kernel = c->ut.valid ? kKernelUniform : kKernelGather;
+    c->ghost.on = (c->kernel == kKernelUniform) && (c->ax.periodic || c->ay.periodic);
   } else {
     c->kernel = kKernelGather;
   }
@@ -495,6 +550,7 @@ sllbm_status sllbm_init_equilibrium(sllbm_ctx* c, const double* rho, const doubl
   a.cp = c->cp;
   a.store = c->store;
   CUDA_TRY(c, launch_init_equilibrium(a, c->stream));
+  CUDA_TRY(c, fill_ghosts(c));
   c->initialized = true;
   return SLLBM_OK;
 }
@@ -540,13 +596,6 @@ int sllbm_launches_per_step(const sllbm_ctx* c) {
   return (c->kernel == kKernelUniform && c->n_fix > 0) ? 2 : 1;
 }
 
-static cudaError_t copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
-  // dense [npop][25][ny][nx] <-> pitched [npop][25][ny][pitch]
-  const size_t row = (size_t)c->nx * c->elem, prow = (size_t)c->pitch * c->elem;
-  const size_t rows = (size_t)c->npop * kQ * c->ny;
-  if (to_internal) return cudaMemcpy2DAsync(dst, prow, src, row, row, rows, kind, c->stream);
-  return cudaMemcpy2DAsync(dst, row, src, prow, row, rows, kind, c->stream);
-}
 
 sllbm_status sllbm_get_state(sllbm_ctx* c, void* dst) {
   if (!c || !dst) return fail(c, SLLBM_ERR_ARG, "null pointer");
@@ -557,6 +606,7 @@ sllbm_status sllbm_get_state(sllbm_ctx* c, void* dst) {
 sllbm_status sllbm_set_state(sllbm_ctx* c, const void* src) {
   if (!c || !src) return fail(c, SLLBM_ERR_ARG, "null pointer");
   CUDA_TRY(c, copy_state(c, c->state[c->cur], src, true, cudaMemcpyDeviceToDevice));
+  CUDA_TRY(c, fill_ghosts(c));
   c->initialized = true;
   return SLLBM_OK;
 }
@@ -565,6 +615,7 @@ sllbm_status sllbm_step_host(sllbm_ctx* c, const void* in, void* out, int nsteps
   if (!c || !in || !out || nsteps < 0) return fail(c, SLLBM_ERR_ARG, "bad arguments");
   if (!c->precomputed) return fail(c, SLLBM_ERR_STATE, "precompute_departures first");
   CUDA_TRY(c, copy_state(c, c->state[c->cur], in, true, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, fill_ghosts(c));
   c->initialized = true;
   for (int k = 0; k < nsteps; ++k) CUDA_TRY(c, enqueue_step(c));
   CUDA_TRY(c, copy_state(c, out, c->state[c->cur], false, cudaMemcpyDeviceToHost));
@@ -598,6 +649,7 @@ sllbm_status sllbm_moments(sllbm_ctx* c, float* rho, float* u, float* v, float* 
   if (me) CUDA_TRY(c, cudaMemcpyAsync(me, c->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (flag & 4) return fail(c, SLLBM_ERR_CUDA, "a staging copy of the fused kernel timed out");
   if (flag & 1) return fail(c, SLLBM_ERR_UNSTABLE, "non-positive or non-finite density/temperature");
   return SLLBM_OK;
 }

@@ -41,17 +41,21 @@ struct StepArgs {
   // optional vertex list (gather kernel only): process vlist[0..nlist) instead of every vertex
   const int* vlist;
   long long nlist;
+  GhostK ghost;         // periodic images to keep up to date in the ghost cells
 };
 
 // Cell-periodic pattern of a uniform grid (see step_uniform.cu): per velocity component and
 // local node, the y interpolation as a band of 2p+1 taps around the vertex and the x taps.
 struct UniformTables {
   bool valid;
-  float wy_band[kQ1][4][9];   // [b][l][j]: weight of source row y + j - p for local row l
+  bool tall;                  // 16-row tiles (one CTA per SM) or 8-row tiles (two per SM)
+  float wy_pat[kQ1][4][5];    // [b][l][alpha]
   float wx_pat[kQ1][4][5];    // [a][k][alpha]
-  int dx_pat[kQ1][4];         // [a][k]: stencil start - vertex
+  int dy_pat[kQ1][4];         // [b][l]: stencil start - vertex row, in [-p, 0]
+  int dx_pat[kQ1][4];         // [a][k]: stencil start - vertex column, in [-p, 0]
   const unsigned char* std_x; // [nx]: column follows the pattern
   const unsigned char* std_y; // [ny]
+  int gx, gy, rows_alloc;     // ghost columns/rows before the interior origin; rows per plane
 };
 
 // Generic FP32 gather step (one thread per vertex, (p+1)^2 gathers per plane from L1/L2).
@@ -59,7 +63,7 @@ cudaError_t launch_step_gather(const StepArgs& a, int store, cudaStream_t s);
 // Fused shared-memory step for uniform grids (pattern band interpolation); writes only the
 // vertices marked in std_x/std_y.  cudaErrorNotSupported if the tables are not valid.
 cudaError_t launch_step_uniform(const StepArgs& a, const UniformTables& t, int store, cudaStream_t s);
-int uniform_tile_rows(int P);
+int uniform_tile_rows(int P, bool tall);
 // Plain FP64 step on full populations.
 cudaError_t launch_step_plain_f64(const StepArgs& a, cudaStream_t s);
 
@@ -91,6 +95,10 @@ struct InitArgs {
   int store;
 };
 cudaError_t launch_init_equilibrium(const InitArgs& a, cudaStream_t s);
+// Copy the periodic images of interior vertices into the ghost cells of `planes` planes (clamped
+// copies on non-periodic axes).  `origin`: interior origin of plane 0; elem: bytes per element.
+cudaError_t launch_ghost_fill(void* origin, int elem, size_t plane_stride, int pitch, int planes,
+                              const GhostK& g, cudaStream_t s);
 
 // ---- moments and reductions ----
 struct MomentArgs {

@@ -263,4 +263,60 @@ cudaError_t launch_init_equilibrium(const InitArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// Ghost cells: rows [ylo, 0) and [ny, yhi) over all kept columns, and columns [xlo, 0), [nx, xhi)
+// of the interior rows, copied from their periodic (or clamped) source vertex.
+// ------------------------------------------------------------------------------------------
+template <typename E>
+__global__ void ghost_fill_kernel(E* origin, size_t plane_stride, int pitch, int planes, GhostK g) {
+  const long long W = g.xhi - g.xlo, topb = -g.ylo + (g.yhi - g.ny), side = -g.xlo + (g.xhi - g.nx);
+  const long long per_plane = topb * W + (long long)g.ny * side;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per_plane * planes) return;
+  const int plane = (int)(t / per_plane);
+  long long e = t - (long long)plane * per_plane;
+  int xx, yy;
+  if (e < topb * W) {
+    const int r = (int)(e / W), c = (int)(e - (long long)r * W);
+    yy = r < -g.ylo ? g.ylo + r : g.ny + (r + g.ylo);
+    xx = g.xlo + c;
+  } else {
+    e -= topb * W;
+    const int r = (int)(e / side), c = (int)(e - (long long)r * side);
+    yy = r;
+    xx = c < -g.xlo ? g.xlo + c : g.nx + (c + g.xlo);
+  }
+  int sx = xx, sy = yy;
+  if (g.px) {
+    sx %= g.nx;
+    if (sx < 0) sx += g.nx;
+  } else {
+    sx = sx < 0 ? 0 : (sx >= g.nx ? g.nx - 1 : sx);
+  }
+  if (g.py) {
+    sy %= g.ny;
+    if (sy < 0) sy += g.ny;
+  } else {
+    sy = sy < 0 ? 0 : (sy >= g.ny ? g.ny - 1 : sy);
+  }
+  E* pl = origin + (ptrdiff_t)plane * plane_stride;
+  pl[(ptrdiff_t)yy * pitch + xx] = pl[(ptrdiff_t)sy * pitch + sx];
+}
+
+cudaError_t launch_ghost_fill(void* origin, int elem, size_t plane_stride, int pitch, int planes,
+                              const GhostK& g, cudaStream_t s) {
+  const long long W = g.xhi - g.xlo, topb = -g.ylo + (g.yhi - g.ny), side = -g.xlo + (g.xhi - g.nx);
+  const long long n = (topb * W + (long long)g.ny * side) * planes;
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  switch (elem) {
+    case 2: ghost_fill_kernel<uint16_t><<<blocks, threads, 0, s>>>(static_cast<uint16_t*>(origin), plane_stride, pitch, planes, g); break;
+    case 4: ghost_fill_kernel<uint32_t><<<blocks, threads, 0, s>>>(static_cast<uint32_t*>(origin), plane_stride, pitch, planes, g); break;
+    case 8: ghost_fill_kernel<uint64_t><<<blocks, threads, 0, s>>>(static_cast<uint64_t*>(origin), plane_stride, pitch, planes, g); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace sllbm

@@ -68,13 +68,15 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
   }
   const bool ok = collide_deviation_f32(vals, a.cs, a.cp);
   if (!ok) atomicOr(a.flag, 1);
-  const size_t o = (size_t)iy * a.pitch + ix;
+  store_images(a.ghost, ix, iy, [&](int xx, int yy) {
+    const ptrdiff_t o = (ptrdiff_t)yy * a.pitch + xx;
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) st_store(dst + (size_t)i * a.plane_stride + o, vals[i]);
-  if (a.cp.npop == 2) {
+    for (int i = 0; i < kQ; ++i) st_store(dst + (ptrdiff_t)i * a.plane_stride + o, vals[i]);
+    if (a.cp.npop == 2) {
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) st_store(dst + (size_t)(kQ + i) * a.plane_stride + o, vals[kQ + i]);
-  }
+      for (int i = 0; i < kQ; ++i) st_store(dst + (ptrdiff_t)(kQ + i) * a.plane_stride + o, vals[kQ + i]);
+    }
+  });
 }
 
 template <int P, typename Store>
