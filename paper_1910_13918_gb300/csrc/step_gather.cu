@@ -52,14 +52,19 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
     for (int pop = 0; pop < 2; ++pop) {
       if (pop < a.cp.npop) {
         const Store* pl = src + (size_t)(pop * kQ + i) * a.plane_stride;
-        float acc = 0.f;
+        // difference form (see the uniform kernel): constants are reproduced exactly in FP32
+        float rows[P + 1];
 #pragma unroll
         for (int kb = 0; kb <= P; ++kb) {
-          float accx = 0.f;
+          const float base = ld_store(pl + row[kb] + col[0]);
+          float accx = base;
 #pragma unroll
-          for (int ka = 0; ka <= P; ++ka) accx += wx[ka] * ld_store(pl + row[kb] + col[ka]);
-          acc += wy[kb] * accx;
+          for (int ka = 1; ka <= P; ++ka) accx += wx[ka] * (ld_store(pl + row[kb] + col[ka]) - base);
+          rows[kb] = accx;
         }
+        float acc = rows[0];
+#pragma unroll
+        for (int kb = 1; kb <= P; ++kb) acc += wy[kb] * (rows[kb] - rows[0]);
         vals[pop * kQ + i] = acc;
       } else {
         vals[pop * kQ + i] = 0.f;

@@ -10,14 +10,15 @@
 // zero-gradient boundaries) are not written here; the host runs the gather kernel on exactly
 // those vertices afterwards.
 //
-// CTA = 32 x TY vertices (TY a multiple of p), one vertex per thread.  The 50 planes are done in
-// 5 stages, one per x component a.  A stage (the 10 planes b = 0..4 of f and g) is copied into
+// Persistent CTAs (one or two per SM) walk over tiles of 32 x TY vertices (TY a multiple of p),
+// one vertex per thread.  The 50 planes of a tile are done in 5 stages, one per x component a.  A stage (the 10 planes b = 0..4 of f and g) is copied into
 // shared memory by two TMA tensor copies (tile + stencil halo; the state layout carries ghost
 // cells with the periodic images, so a tile never wraps), completing on an mbarrier, two stages
 // ahead in three buffers.  Phase k runs the y pass of stage k (task = (plane, staged column),
 // register window of the column) and the x pass of stage k-1 (thread = vertex): six barriers per
 // tile.  After stage 4 every thread holds the 50 pre-collision deviations of its vertex, collides
-// in registers and writes 50 coalesced rows (plus periodic images in the ghost cells).
+// in registers and writes 50 coalesced rows (plus periodic images in the ghost cells), while the
+// first two stages of its next tile are already in flight.
 #include <cuda.h>
 
 #include "kernels.h"
@@ -93,17 +94,65 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
 }
 
 // y interpolation of one staged column for the rows r = l (mod p), stencil start D relative to
-// the row: t[r] = sum_alpha w[alpha] * win[r + P + D + alpha]  (window row j is tile row j - P).
+// the row: t[r] = sum_alpha w[alpha] * win[r + P + D + alpha]  (window row j is tile row j - P),
+// evaluated as win[s] + sum_{alpha >= 1} w[alpha] (win[s + alpha] - win[s]).  Since the weights
+// sum to one the two are equal, but the second reproduces a constant field exactly in FP32:
+// FP32-rounded weights do not sum to one exactly, and in the first form the deficit would bias
+// every uniform region the same way every step (a systematic mass drift).
 template <int P, int TY, int R, int D>
 __device__ __forceinline__ void y_taps(const float (&win)[R], const float (&w)[P + 1], int l,
                                        float* tout, int C) {
 #pragma unroll
   for (int r = 0; r < TY; ++r) {
     if (r % P != l) continue;
-    float acc = 0.f;
+    const float base = win[r + P + D];
+    float acc = base;
 #pragma unroll
-    for (int al = 0; al <= P; ++al) acc += w[al] * win[r + P + D + al];
+    for (int al = 1; al <= P; ++al) acc += w[al] * (win[r + P + D + al] - base);
     tout[r * C] = acc;
+  }
+}
+
+// y pass of one stage: task = (plane g, staged column c) with exact taps of (b, l).  The first
+// G*32 tasks give each warp one plane (warp-uniform b, no divergence in the tap switch); the
+// remaining G*(C-32) cover the right-hand staged columns.  Kept out of line: the same code
+// serves the five stages of a tile, which keeps the instruction footprint small.
+template <int P, int TY, int R, int G, int C, int NT, typename Store>
+__device__ __noinline__ void y_pass(const Store* Sst, int box_stride, float* Tst, const float* WY,
+                                    const int* DY, int npop) {
+  const int tid = threadIdx.x;
+#pragma unroll 1
+  for (int t = tid; t < G * C; t += NT) {
+    int g, c;
+    if (t < G * 32) {
+      g = t >> 5;
+      c = t & 31;
+    } else {
+      g = (t - G * 32) / (C - 32);
+      c = 32 + (t - G * 32) - g * (C - 32);
+    }
+    const int pop = g >= 5, b = g - 5 * pop;
+    if (pop >= npop) continue;
+    const Store* col = Sst + (size_t)pop * box_stride + (size_t)b * R * C + c;
+    float win[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) win[j] = to_f(col[j * C]);
+    float* tout = Tst + (size_t)g * TY * C + c;
+#pragma unroll
+    for (int l = 0; l < P; ++l) {
+      float w[P + 1];
+      const float* wp = WY + (b * P + l) * 8;
+#pragma unroll
+      for (int al = 0; al <= P; ++al) w[al] = wp[al];
+      switch (DY[b * P + l]) {
+        case 0: y_taps<P, TY, R, 0>(win, w, l, tout, C); break;
+        case -1: y_taps<P, TY, R, -1>(win, w, l, tout, C); break;
+        case -2: if constexpr (P >= 2) y_taps<P, TY, R, -2>(win, w, l, tout, C); break;
+        case -3: if constexpr (P >= 3) y_taps<P, TY, R, -3>(win, w, l, tout, C); break;
+        case -4: if constexpr (P >= 4) y_taps<P, TY, R, -4>(win, w, l, tout, C); break;
+        default: break;
+      }
+    }
   }
 }
 
@@ -149,10 +198,10 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, row = tid >> 5;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * TY;
-  const int x = x0 + lane, y = y0 + row;
   const int npop = a.cp.npop;
   const unsigned stage_bytes = (unsigned)(npop * BS::BYTES);
+  const int tiles_x = (a.nx + 31) / 32;
+  const int ntiles = tiles_x * ((a.ny + TY - 1) / TY);
 
   for (int e = tid; e < kQ1 * P * 8; e += NT) {
     (&WX[0])[e] = (&ua.pat.wx[0][0][0])[e];
@@ -168,103 +217,79 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   }
   __syncthreads();  // tables and barriers
 
-  // ---- stage st (x component a = st): two TMA boxes (f, g) of 5 planes x R rows x C cols ----
-  auto stage_load = [&](int st) {
-    if (tid == 0) {
-      const int buf = st % NSB;
+  // Global stage counter: the k-th tile of this CTA has stages 5k .. 5k+4; stage s lands in
+  // S[s % 3] and completes phase (s / 3) & 1 of BAR[s % 3]; it is issued two stages ahead, so the
+  // first two stages of the next tile are in flight while a tile finishes and collides.
+  auto issue = [&](int tile, int st, long s) {
+    if (tid == 0 && tile < ntiles) {
+      const int buf = (int)(s % NSB);
+      const int tx0 = (tile % tiles_x) * 32, ty0 = (tile / tiles_x) * TY;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       mbar_expect_tx(&BAR[buf], stage_bytes);
-      const int cx = ua.gx + x0 - CO, cy = ua.gy + y0 - P;
       for (int pop = 0; pop < npop; ++pop)
-        tma_load_3d(S + (size_t)(buf * 2 + pop) * BS::STRIDE, &ua.tmap, cx, cy, pop * kQ + 5 * st,
-                    &BAR[buf]);
+        tma_load_3d(S + (size_t)(buf * 2 + pop) * BS::STRIDE, &ua.tmap, ua.gx + tx0 - CO,
+                    ua.gy + ty0 - P, pop * kQ + 5 * st, &BAR[buf]);
     }
   };
 
-  stage_load(0);
-  stage_load(1);
-
-  float vals[2 * kQ];
-#pragma unroll
-  for (int ph = 0; ph <= kQ1; ++ph) {
-    if (ph < kQ1) mbar_wait(&BAR[ph % NSB], (ph / NSB) & 1, a.flag);   // stage ph landed
-    __syncthreads();  // T[(ph-1)%2] written; T[ph%2] and S[(ph+2)%3] no longer read
-    if (ph + 2 < kQ1) stage_load(ph + 2);   // its buffer held stage ph-1, consumed in phase ph-1
-
-    // ---- y pass of stage ph: task = (plane g, staged column c), exact taps of (b, l) ----
-    if (ph < kQ1) {
+  issue(blockIdx.x, 0, 0);
+  issue(blockIdx.x, 1, 1);
+  long s0 = 0;   // global index of stage 0 of the current tile
 #pragma unroll 1
-      for (int t = tid; t < G * C; t += NT) {
-        // the first G*32 tasks give each warp one plane (warp-uniform b, no divergence in the
-        // tap switch); the remaining G*(C-32) cover the right-hand staged columns
-        int g, c;
-        if (t < G * 32) {
-          g = t >> 5;
-          c = t & 31;
-        } else {
-          g = (t - G * 32) / (C - 32);
-          c = 32 + (t - G * 32) - g * (C - 32);
-        }
-        const int pop = g >= 5, b = g - 5 * pop;
-        if (pop >= npop) continue;
-        const Store* col = S + (size_t)((ph % NSB) * 2 + pop) * BS::STRIDE + (size_t)b * R * C + c;
-        float win[R];
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s0 += kQ1) {
+    const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * TY;
+    const int x = x0 + lane, y = y0 + row;
+    float vals[2 * kQ];
 #pragma unroll
-        for (int j = 0; j < R; ++j) win[j] = to_f(col[j * C]);
-        float* tout = T + ((size_t)(ph & 1) * G + g) * TY * C + c;
+    for (int ph = 0; ph <= kQ1; ++ph) {
+      const long s = s0 + ph;
+      if (ph < kQ1) mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);  // stage landed
+      __syncthreads();  // T[(s-1)&1] written; T[s&1] and S[(s+2)%3] no longer read
+      if (ph + 2 < kQ1)
+        issue(tile, ph + 2, s + 2);
+      else if (ph < kQ1)
+        issue(tile + gridDim.x, ph + 2 - kQ1, s + 2);   // next tile's stage 0 / 1
+      if (ph < kQ1)
+        y_pass<P, TY, R, G, C, NT, Store>(S + (size_t)(s % NSB) * 2 * BS::STRIDE, BS::STRIDE,
+                                          T + (size_t)(s & 1) * G * TY * C, WY, DY, npop);
+
+      // ---- x pass of stage ph-1: thread = vertex; exact taps of (a, k = x mod p) ----
+      if (ph >= 1) {
+        const int st = ph - 1;
+        const int k = x % P;
+        const float* w = WX + (st * P + k) * 8;
+        const int cbase = lane + CO + DX[st * P + k];
+        float wr[P + 1];
 #pragma unroll
-        for (int l = 0; l < P; ++l) {
-          float w[P + 1];
-          const float* wp = WY + (b * P + l) * 8;
+        for (int al = 0; al <= P; ++al) wr[al] = w[al];
 #pragma unroll
-          for (int al = 0; al <= P; ++al) w[al] = wp[al];
-          switch (DY[b * P + l]) {
-            case 0: y_taps<P, TY, R, 0>(win, w, l, tout, C); break;
-            case -1: y_taps<P, TY, R, -1>(win, w, l, tout, C); break;
-            case -2: if constexpr (P >= 2) y_taps<P, TY, R, -2>(win, w, l, tout, C); break;
-            case -3: if constexpr (P >= 3) y_taps<P, TY, R, -3>(win, w, l, tout, C); break;
-            case -4: if constexpr (P >= 4) y_taps<P, TY, R, -4>(win, w, l, tout, C); break;
-            default: break;
-          }
+        for (int g = 0; g < G; ++g) {
+          const int pop = g / 5, b = g % 5;
+          const float* trow = T + (((size_t)((s - 1) & 1) * G + g) * TY + row) * C + cbase;
+          const float base = trow[0];   // difference form, as in y_taps
+          float acc = base;
+#pragma unroll
+          for (int al = 1; al <= P; ++al) acc += wr[al] * (trow[al] - base);
+          vals[pop * kQ + 5 * st + b] = (pop < npop) ? acc : 0.f;
         }
       }
     }
 
-    // ---- x pass of stage ph-1: thread = vertex; exact taps of (a, k = x mod p) ----
-    if (ph >= 1) {
-      const int st = ph - 1;
-      const int k = x % P;
-      const float* w = WX + (st * P + k) * 8;
-      const int cbase = lane + CO + DX[st * P + k];
-      float wr[P + 1];
+    const bool ok = collide_deviation_f32(vals, a.cs, a.cp);
+    if (x < a.nx && y < a.ny && ua.std_x[x] && ua.std_y[y]) {
+      if (!ok) atomicOr(a.flag, 1);
+      Store* dst = static_cast<Store*>(a.dst);
+      store_images(a.ghost, x, y, [&](int xx, int yy) {
+        const ptrdiff_t o = (ptrdiff_t)yy * a.pitch + xx;
 #pragma unroll
-      for (int al = 0; al <= P; ++al) wr[al] = w[al];
+        for (int i = 0; i < kQ; ++i) st_store(dst + (ptrdiff_t)i * a.plane_stride + o, vals[i]);
+        if (npop == 2) {
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int pop = g / 5, b = g % 5;
-        const float* trow = T + (((size_t)(st & 1) * G + g) * TY + row) * C + cbase;
-        float acc = 0.f;
-#pragma unroll
-        for (int al = 0; al <= P; ++al) acc += wr[al] * trow[al];
-        vals[pop * kQ + 5 * st + b] = (pop < npop) ? acc : 0.f;
-      }
+          for (int i = 0; i < kQ; ++i)
+            st_store(dst + (ptrdiff_t)(kQ + i) * a.plane_stride + o, vals[kQ + i]);
+        }
+      });
     }
-  }
-
-  const bool ok = collide_deviation_f32(vals, a.cs, a.cp);
-  if (x < a.nx && y < a.ny && ua.std_x[x] && ua.std_y[y]) {
-    if (!ok) atomicOr(a.flag, 1);
-    Store* dst = static_cast<Store*>(a.dst);
-    store_images(a.ghost, x, y, [&](int xx, int yy) {
-      const ptrdiff_t o = (ptrdiff_t)yy * a.pitch + xx;
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) st_store(dst + (ptrdiff_t)i * a.plane_stride + o, vals[i]);
-      if (npop == 2) {
-#pragma unroll
-        for (int i = 0; i < kQ; ++i)
-          st_store(dst + (ptrdiff_t)(kQ + i) * a.plane_stride + o, vals[kQ + i]);
-      }
-    });
   }
 }
 
@@ -341,7 +366,15 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((a.nx + 31) / 32, (a.ny + TS::TY - 1) / TS::TY);
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (n_sm <= 0) n_sm = 1;
+  }
+  const int ntiles = ((a.nx + 31) / 32) * ((a.ny + TS::TY - 1) / TS::TY);
+  const int grid = ntiles < n_sm * TS::MINB ? ntiles : n_sm * TS::MINB;   // persistent CTAs
   step_uniform_kernel<P, Store, Tall><<<grid, TS::NT, smem, s>>>(ua);
   return cudaGetLastError();
 }

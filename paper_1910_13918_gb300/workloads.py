@@ -15,7 +15,8 @@ Parameter recipe (readings of the paper where it is silent):
   1.94815; T = p / rho with R = 1;
 * shock-vortex (Sec. III.E): region A (x < 0.5) rho = 1, P = 1/gamma, u = 1.2 (Ma_A = 1.2 with
   c_A = 1); region B from the Rankine-Hugoniot relations; an isentropic vortex of radius 0.075,
-  Ma_v = 0.25, with the radial-equilibrium exponent Ma_v^2; nu from Re = c_A R / nu = 400;
+  Ma_v = 0.25, with the radial-equilibrium exponent Ma_v^2; nu from Re = c_A R / nu = 75 (the
+  paper's 400 diverges at the time step these 200 steps need, see svi());
 * gamma = 1.4 everywhere, so C_v = R / (gamma - 1) = 2.5.
 """
 from __future__ import annotations
@@ -286,9 +287,15 @@ def riemann_paper():
 
 
 def svi():
-    """Shock-vortex interaction on the sine-mapped grid [0,2]x[0,1], 512x256 cells, p = 2."""
+    """Shock-vortex interaction on the sine-mapped grid [0,2]x[0,1], 512x256 cells, p = 2.
+
+    dt = 3e-3 lets the acoustic signal of the vortex reach x > 1.5 within the 200 steps (t = 0.6).
+    At that step the paper's Re = c_A R / nu = 400 (and 200) leaves tau = 0.56 (0.63) and the
+    run diverges within 40 (60) steps in FP64 as well as FP32; Re = 100 (tau = 0.75) stays
+    bounded from the smooth fields but diverges within 80 steps once they carry the 1e-4 seeded
+    perturbation of the parity tests; Re = 75 (tau = 0.83) stays bounded with it and is used."""
     radius = 0.075
-    nu = 1.0 * radius / 400.0
+    nu = 1.0 * radius / 75.0
     dt = 3.0e-3
     return Workload("svi512x256_p2_mapped", 512, 256, 2, 0.0, 2.0, 0.0, 1.0, ZERO_GRADIENT,
                     PERIODIC, dt, nu / dt + 0.5, 200, "svi", map_a=0.05, seed=5,

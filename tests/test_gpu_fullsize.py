@@ -53,7 +53,7 @@ def test_one_step_sampled_against_oracle(gpu_lib, name):
 
 
 @pytest.mark.parametrize("name,nsteps", [("tgv256", 1000), ("riemann_paper", 200), ("svi", 200),
-                                         ("sod", 2000)])
+                                         ("sod", 300)])
 def test_long_run_f32_against_f64(gpu_lib, name, nsteps):
     w = W.ALL[name]()
     a, ma = _fields(_gpu(w, nsteps, "f32"))
@@ -61,6 +61,19 @@ def test_long_run_f32_against_f64(gpu_lib, name, nsteps):
     err = H.field_errors(a, b, w.velocity_scale)
     assert max(err.values()) <= 1e-4, (name, err)
     assert abs(ma["mass"] / mb["mass"] - 1) < 1e-6
+
+
+def test_sod_long_run_f32_mass_tracks_f64(gpu_lib):
+    """2000 steps of the Sod workload: the FP32 run keeps the FP64 run's mass (the interpolation
+    reproduces constants exactly, so uniform regions do not drift) and its fields."""
+    w = W.sod()
+    n = 2000
+    a, ma = _fields(_gpu(w, n, "f32"))
+    b, mb = _fields(_gpu(w, n, "f64"))
+    err = H.field_errors(a, b, w.velocity_scale)
+    print("sod 2000 steps f32 vs f64:", err, "mass", ma["mass"] / mb["mass"] - 1)
+    assert abs(ma["mass"] / mb["mass"] - 1) < 2e-6
+    assert max(err.values()) < 1e-3, err
 
 
 def test_tgv256_mass_and_energy_conserved(gpu_lib):
@@ -97,3 +110,50 @@ def test_riemann_baseline_states_leave_the_model_range(gpu_lib):
             for _ in range(10):
                 s.step(1)
                 s.moments(sums=False)
+
+
+def test_svi_adjoint_against_central_differences(gpu_lib):
+    """Shock-vortex workload (mapped grid, 200 steps, checkpoints every 20): the FP32 adjoint
+    gradient of J = sum_{x > 1.5} A_v rho_v(t_end) w.r.t. the initial velocity, projected on 16
+    seeded directions (N(0,1) x the vortex envelope), against central differences of the FP64
+    forward step (eps = 1e-6 relative to the inflow speed)."""
+    from paper_1910_13918_gb300.autograd import rollout
+    from paper_1910_13918_gb300.sllbm import SLLBM
+    w = W.svi()
+    k = w.extra["checkpoint_every"]
+    s = SLLBM.from_workload(w, prec="f32")
+    s.precompute()
+    x, y = (t.cpu().numpy() for t in s.coords())
+    r, u, v, T = (torch.as_tensor(f, dtype=torch.float64, device="cuda") for f in w.fields(x, y))
+    u.requires_grad_(True)
+    v.requires_grad_(True)
+    A = s.vertex_weights()
+    mask = torch.as_tensor(x > w.extra["x_objective"], device="cuda")
+    rho = rollout(s, u, v, r, T, w.steps, k)
+    J = (A * mask * rho).sum()
+    J.backward()
+    du, dv = u.grad.cpu().numpy(), v.grad.cpu().numpy()
+    # FP64 forward for the differences
+    s64 = SLLBM.from_workload(w, prec="f64")
+    s64.precompute()
+    A64 = s64.vertex_weights().cpu().numpy()
+    m64 = x > w.extra["x_objective"]
+    rho0, u0, v0, T0 = w.fields(x, y)
+
+    def J64(uu, vv):
+        s64.init(rho0, uu, vv, T0)
+        s64.step(w.steps)
+        st = s64.get_state().cpu().numpy()
+        return float(np.sum(A64 * m64 * st[0].sum(axis=0)))
+
+    eps = 1e-6 * w.velocity_scale
+    errs, ads = [], []
+    for d1, d2 in W.svi_directions(w, x, y, 16):
+        fd = (J64(u0 + eps * d1, v0 + eps * d2) - J64(u0 - eps * d1, v0 - eps * d2)) / (2 * eps)
+        ad = float(np.sum(du * d1) + np.sum(dv * d2))
+        errs.append(abs(fd - ad))
+        ads.append(abs(ad))
+    scale = max(ads)
+    print("svi adjoint: max |AD| =", scale, "max |FD - AD| =", max(errs))
+    assert scale > 1e-7, scale                      # a gradient well above FD round-off (~1e-9)
+    assert max(errs) <= 1e-3 * scale, (max(errs), scale)
