@@ -165,6 +165,26 @@ sllbm_status sllbm_init_equilibrium_vjp(sllbm_ctx* ctx, const double* rho_dev, c
                                         const double* v_dev, const double* T_dev,
                                         const float* lambda0_dev, float* du_dev, float* dv_dev);
 
+/* Allocation-free moments and mass/energy sums.  The paper has no counterpart; this is for
+ * callers that must not allocate device memory: code running inside a framework whose caching
+ * allocator has reserved the device memory (a cudaMalloc beside it can fail or fragment),
+ * latency-critical loops (cudaFree synchronises the whole device), or callers with a fixed memory
+ * budget.  It computes what sllbm_moments computes, without a context:
+ *   state_dev: FP32 deviation state in the dense layout of sllbm_get_state, [n_pop][25][ny][nx]
+ *              with n_pop = 1 if cv == 1, else 2 (caller-owned, device);
+ *   A_dev:     vertex weights (sllbm_vertex_weights, nx*ny doubles) or NULL to skip the sums;
+ *   rho/u/v/T: FP32 outputs of nx*ny floats, each may be NULL;
+ *   mass_energy_dev: two doubles on the device, written only if A_dev is given.
+ * Its reduction scratch is a file-scope device array of 1 MiB (the library keeps it on every GPU
+ * that loads it until the process exits), so grids are limited to 16,777,216 vertices
+ * (SLLBM_ERR_UNSUPPORTED beyond).  The first call on a device looks up that array's address;
+ * make that first call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race; serialise them.  Synchronises
+ * cuda_stream; returns SLLBM_ERR_UNSTABLE like sllbm_moments. */
+sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, int ny, double cv,
+                                   const double* A_dev, float* rho_dev, float* u_dev, float* v_dev,
+                                   float* T_dev, double* mass_energy_dev, void* cuda_stream);
+
 /* Name of the kernel the step uses for this context ("uniform_fused", "gather", "plain_f64"). */
 const char* sllbm_step_kernel_name(const sllbm_ctx* ctx);
 

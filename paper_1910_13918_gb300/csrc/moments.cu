@@ -112,3 +112,83 @@ cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s) {
 }
 
 }  // namespace sllbm
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of the moments / mass-energy reduction (sllbm_moments_noalloc).
+//
+// The reduction needs per-block FP64 partials and an instability flag.  Here they live in a
+// file-scope device array instead of memory the caller or a context allocates.  Every GPU that
+// loads the library holds this array until the process exits.  In host code the symbol is only
+// a stand-in, so its device address is looked up once per device with cudaGetSymbolAddress.
+// ------------------------------------------------------------------------------------------
+#include <math.h>
+
+#include "../../include/sllbm.h"
+
+namespace sllbm {
+
+constexpr int kNoAllocMaxBlocks = 65536;   // => at most 65536 * 256 = 16,777,216 vertices
+// layout: [0, 2 * kNoAllocMaxBlocks) doubles of partials, then one int flag (in a double slot)
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxBlocks + 2];
+
+constexpr int kMaxDevices = 64;
+static double* g_noalloc_ptr[kMaxDevices];   // device address of the array, per device
+
+static cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace sllbm
+
+extern "C" sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, int ny, double cv,
+                                              const double* A_dev, float* rho_dev, float* u_dev,
+                                              float* v_dev, float* T_dev, double* mass_energy_dev,
+                                              void* cuda_stream) {
+  using namespace sllbm;
+  if (!state_dev || !mass_energy_dev || nx < 1 || ny < 1 || !(cv >= 1.0)) return SLLBM_ERR_ARG;
+  const long long nv = (long long)nx * ny;
+  if (moments_blocks(nv) > kNoAllocMaxBlocks) return SLLBM_ERR_UNSUPPORTED;   // > 16,777,216 vertices
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return SLLBM_ERR_CUDA;
+  int* flag = reinterpret_cast<int*>(scratch + 2 * kNoAllocMaxBlocks);
+  if (cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) return SLLBM_ERR_CUDA;  // starts at zero
+  MomentArgs a{};
+  a.src = state_dev;
+  a.nx = nx;
+  a.ny = ny;
+  a.pitch = nx;
+  a.nv = nv;
+  a.plane_stride = (size_t)nv;
+  const double s10 = sqrt(10.0), sm = sqrt(5.0 - s10), lg = sqrt(5.0 + s10);
+  const double xi[5] = {0.0, sm, lg, -sm, -lg};
+  for (int k = 0; k < 5; ++k) a.cs.xi[k] = xi[k];
+  a.cp.cv = cv;
+  a.cp.npop = (cv == 1.0) ? 1 : 2;
+  a.store = kStoreF32;
+  a.A = A_dev;
+  a.rho = rho_dev;
+  a.u = u_dev;
+  a.v = v_dev;
+  a.T = T_dev;
+  a.partials = A_dev ? scratch : nullptr;   // the block partials are all overwritten: no clearing
+  a.sums = mass_energy_dev;
+  a.flag = flag;
+  if (launch_moments(a, s) != cudaSuccess) return SLLBM_ERR_CUDA;
+  int host_flag = 0;
+  if (cudaMemcpyAsync(&host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return SLLBM_ERR_CUDA;
+  return (host_flag & 1) ? SLLBM_ERR_UNSTABLE : SLLBM_OK;
+}

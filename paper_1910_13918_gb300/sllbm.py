@@ -27,7 +27,7 @@ EXPORTS = [
     "sllbm_vertex_coords", "sllbm_vertex_weights", "sllbm_precompute_departures",
     "sllbm_init_equilibrium", "sllbm_step", "sllbm_step_host", "sllbm_moments", "sllbm_get_state",
     "sllbm_set_state", "sllbm_adjoint_step", "sllbm_init_equilibrium_vjp", "sllbm_step_kernel_name",
-    "sllbm_launches_per_step", "sllbm_status_string", "sllbm_last_error",
+    "sllbm_launches_per_step", "sllbm_status_string", "sllbm_last_error", "sllbm_moments_noalloc",
 ]
 
 
@@ -83,6 +83,7 @@ def load(path: str | None = None):
         "sllbm_step_kernel_name": ([P], ctypes.c_char_p),
         "sllbm_launches_per_step": ([P], I),
         "sllbm_status_string": ([I], ctypes.c_char_p),
+        "sllbm_moments_noalloc": ([V, I, I, D, V, V, V, V, V, V, P], I),
         "sllbm_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
