@@ -30,7 +30,10 @@ UNIT = "GVUPS"
 
 # DRAM traffic (read + write bytes per launch) of the step kernel from an ncu capture, keyed by
 # (kernel source digest, workload, precision); reported as null once the kernel source changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/step_uniform_tgv256_p4_f32.md: 215.6 MB read + 172.6 MB written
+    ("5b7ab0fbe4dbbe7f", "tgv256_p4", "f32"): 388.1e6,
+}
 
 
 def _kernel_digest():
@@ -103,6 +106,19 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value: float) -> float:
+    """Max of a per-rank float over the default process group (identity without one).  The
+    tensor lives on the GPU under NCCL and on the CPU under gloo."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _workload(name):
     from paper_1910_13918_gb300 import workloads as W
     return W.ALL[name]()
@@ -116,59 +132,69 @@ def _workload_desc(w):
 # -------------------------------------------------------------------------------------------------
 # CPU oracle baseline (bounded sample of the same workload)
 # -------------------------------------------------------------------------------------------------
-def oracle_sample_step_time(w, rows=16):
-    """Seconds for one oracle step on the first `rows` vertex rows of the workload, and the
-    number of vertices in that sample.  Initial state evaluated only where the stencils reach."""
-    import numpy as np
-    from oracle import sllbm as o
-    ax = o.Axis(w.nx_cells, w.order, w.x0, w.x1, w.bc_x == 0, w.nodes)
-    ay = o.Axis(w.ny_cells, w.order, w.y0, w.y1, w.bc_y == 0, w.nodes)
-    grid = o.Grid(ax, ay, o.SineMap(w.map_a) if w.map_a else None)
-    X, Y = grid.coords()
-    verts = np.arange(min(rows, grid.ny) * grid.nx)
-    # support of the stencils of the sample (setup, not timed)
-    dep0 = o.Departures(grid, w.dt, verts)
-    keys = []
-    for i in range(25):
-        for b in range(grid.p + 1):
-            for a in range(grid.p + 1):
-                keys.append(ay.vertex_of(dep0.cy[i], b) * grid.nx + ax.vertex_of(dep0.cx[i], a))
-    keys = np.unique(np.concatenate(keys))
-    fields = [np.asarray(F).reshape(-1)[keys] for F in w.fields(X, Y)]
-    f0, g0 = o.initial_state(*fields, w.cv)
-    F = np.zeros((25, grid.ny * grid.nx))
-    G = np.zeros((25, grid.ny * grid.nx))
-    F[:, keys] = f0
-    G[:, keys] = g0
-    F = F.reshape(25, grid.ny, grid.nx)
-    G = G.reshape(25, grid.ny, grid.nx)
-    t = time.perf_counter()
-    dep = o.Departures(grid, w.dt, verts)          # the oracle recomputes departures every step
-    fpre = o.stream(F, dep)
-    gpre = o.stream(G, dep)
-    o.collide(fpre, gpre, w.tau, w.cv)
-    return time.perf_counter() - t, len(verts)
+class OracleSample:
+    """The FP64 oracle on a bounded sample of a workload: one step for the first `rows` vertex
+    rows.  Set-up (grid, the initial state where the sample's stencils reach) is done once; each
+    timed step recomputes the departures, streams and collides, as the oracle's step does."""
+
+    def __init__(self, w, rows=16):
+        import numpy as np
+        from oracle import sllbm as o
+        self.o, self.w = o, w
+        ax = o.Axis(w.nx_cells, w.order, w.x0, w.x1, w.bc_x == 0, w.nodes)
+        ay = o.Axis(w.ny_cells, w.order, w.y0, w.y1, w.bc_y == 0, w.nodes)
+        self.grid = grid = o.Grid(ax, ay, o.SineMap(w.map_a) if w.map_a else None)
+        X, Y = grid.coords()
+        self.verts = np.arange(min(rows, grid.ny) * grid.nx)
+        dep0 = o.Departures(grid, w.dt, self.verts)
+        keys = []
+        for i in range(25):
+            for b in range(grid.p + 1):
+                for a in range(grid.p + 1):
+                    keys.append(ay.vertex_of(dep0.cy[i], b) * grid.nx + ax.vertex_of(dep0.cx[i], a))
+        keys = np.unique(np.concatenate(keys))
+        fields = [np.asarray(F).reshape(-1)[keys] for F in w.fields(X, Y)]
+        f0, g0 = o.initial_state(*fields, w.cv)
+        self.F = np.zeros((25, grid.ny * grid.nx))
+        self.G = np.zeros((25, grid.ny * grid.nx))
+        self.F[:, keys] = f0
+        self.G[:, keys] = g0
+        self.F = self.F.reshape(25, grid.ny, grid.nx)
+        self.G = self.G.reshape(25, grid.ny, grid.nx)
+
+    @property
+    def n_vertices(self):
+        return len(self.verts)
+
+    def step_time(self):
+        o, w = self.o, self.w
+        t = time.perf_counter()
+        dep = o.Departures(self.grid, w.dt, self.verts)
+        fpre = o.stream(self.F, dep)
+        gpre = o.stream(self.G, dep)
+        o.collide(fpre, gpre, w.tau, w.cv)
+        return time.perf_counter() - t
 
 
-def cpu_baseline(w):
-    el, nv = oracle_sample_step_time(w)
+def cpu_baseline(w, rows=16, repeats=3):
+    sample = OracleSample(w, rows)
+    el = min(sample.step_time() for _ in range(repeats))
+    nv = sample.n_vertices
     return {"value": nv * 50 / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle step on the first 16 vertex rows ({nv} vertices) of {w.name}, "
-                      f"{el:.2f} s, numpy float64 single thread"}
+            "sample": f"one oracle step on the first {rows} vertex rows ({nv} vertices) of "
+                      f"{w.name}, best of {repeats}: {el:.2f} s, numpy float64, one thread"}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     w = _workload(args.workload)
+    sample = OracleSample(w, rows=16)
     for _ in range(args.warmup):
-        oracle_sample_step_time(w, rows=4)
-    times, nv = [], 0
-    for _ in range(args.steps):
-        el, nv = oracle_sample_step_time(w, rows=4)
-        times.append(el)
+        sample.step_time()
+    times = [sample.step_time() for _ in range(args.steps)]
+    nv = sample.n_vertices
     tot = sum(times)
     value = nv * 50 * len(times) / tot / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -176,8 +202,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": _workload_desc(w), "sample_vertices": nv},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: one oracle step on the first 4 vertex rows "
-                                       f"({nv} vertices) of {w.name}"},
+                             "sample": f"each step: one oracle step on the first 16 vertex rows "
+                                       f"({nv} vertices) of {w.name}, numpy float64, one thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -223,10 +249,7 @@ def run_ours(args):
         clocks = sampler.stop()
         ms = e0.elapsed_time(e1)
         m = s.moments()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms)
     ms_step = ms_max / args.steps
     updates = w.updates_per_step
     value = updates * args.steps * ws / (ms_max * 1e-3) / 1e9
@@ -247,11 +270,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(k):
             s.step_host(a_in, a_out, 1)
-        el = time.perf_counter() - t0
-        te = torch.tensor([el], dtype=torch.float64, device="cuda")
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        el = float(te.item())
+        el = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": updates * k * ws / el / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb,
                "api": "sllbm_step_host (pinned host state in, 1 step, state out)"}
