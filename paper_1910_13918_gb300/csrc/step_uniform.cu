@@ -38,6 +38,8 @@ struct TileShape {
   static constexpr int G = 10;                   // planes per stage
 };
 
+constexpr int kStageBuffers = 3;   // TMA staging buffers per CTA (prefetch distance 2 stages)
+
 template <typename Store>
 struct StoreShape {
   static constexpr int CO = 16 / sizeof(Store);   // staged column origin x0 - CO (16-byte aligned)
@@ -184,7 +186,8 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   using BS = BoxShape<P, Tall, Store>;
   constexpr int TY = TS::TY, NT = TS::NT, R = TS::R, G = TS::G;
   constexpr int C = SS::C, CO = SS::CO;
-  constexpr int NSB = 3;   // staging buffers: stage k lands in S[k % 3], issued two phases ahead
+  constexpr int NSB = kStageBuffers;   // stage k lands in S[k % NSB], issued NSB-1 stages ahead
+  constexpr int PD = NSB - 1;
   const StepArgs& a = ua.a;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem_raw = smem_dyn + ((128 - (smem_u32(smem_dyn) & 127)) & 127);
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   float* WY = WX + kQ1 * P * 8;                                       // [5][P][8]
   int* DX = reinterpret_cast<int*>(WY + kQ1 * P * 8);                 // [5][P]
   int* DY = DX + kQ1 * P;                                             // [5][P]
-  uint64_t* BAR = reinterpret_cast<uint64_t*>(DY + kQ1 * P);         // [3], 8-byte aligned
+  uint64_t* BAR = reinterpret_cast<uint64_t*>(DY + kQ1 * P);         // [NSB], 8-byte aligned
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, row = tid >> 5;
@@ -232,8 +235,8 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
     }
   };
 
-  issue(blockIdx.x, 0, 0);
-  issue(blockIdx.x, 1, 1);
+#pragma unroll
+  for (int k = 0; k < PD; ++k) issue(blockIdx.x, k, k);
   long s0 = 0;   // global index of stage 0 of the current tile
 #pragma unroll 1
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s0 += kQ1) {
@@ -245,10 +248,10 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
       const long s = s0 + ph;
       if (ph < kQ1) mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);  // stage landed
       __syncthreads();  // T[(s-1)&1] written; T[s&1] and S[(s+2)%3] no longer read
-      if (ph + 2 < kQ1)
-        issue(tile, ph + 2, s + 2);
+      if (ph + PD < kQ1)
+        issue(tile, ph + PD, s + PD);
       else if (ph < kQ1)
-        issue(tile + gridDim.x, ph + 2 - kQ1, s + 2);   // next tile's stage 0 / 1
+        issue(tile + gridDim.x, ph + PD - kQ1, s + PD);   // the next tile's first stages
       if (ph < kQ1)
         y_pass<P, TY, R, G, C, NT, Store>(S + (size_t)(s % NSB) * 2 * BS::STRIDE, BS::STRIDE,
                                           T + (size_t)(s & 1) * G * TY * C, WY, DY, npop);
@@ -301,8 +304,8 @@ static size_t smem_bytes() {
   using TS = TileShape<P, Tall>;
   using SS = StoreShape<Store>;
   using BS = BoxShape<P, Tall, Store>;
-  return 128 + sizeof(Store) * 3 * 2 * BS::STRIDE + sizeof(float) * 2 * TS::G * TS::TY * SS::C +
-         sizeof(float) * 2 * kQ1 * P * 8 + sizeof(int) * (2 * kQ1 * P + 2) + sizeof(uint64_t) * 3;
+  return 128 + sizeof(Store) * kStageBuffers * 2 * BS::STRIDE + sizeof(float) * 2 * TS::G * TS::TY * SS::C +
+         sizeof(float) * 2 * kQ1 * P * 8 + sizeof(int) * (2 * kQ1 * P + 2) + sizeof(uint64_t) * kStageBuffers;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
