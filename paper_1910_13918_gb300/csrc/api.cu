@@ -21,9 +21,15 @@ struct sllbm_ctx {
   sllbm_grid_desc g;
   sllbm_params p;
   cudaStream_t stream = nullptr;
-  int nx = 0, ny = 0, npop = 2, P = 0, pitch = 0, store = kStoreF32, elem = 4;
+  int nx = 0, ny = 0, npop = 2, P = 0, store = kStoreF32, elem = 4;
   long long nv = 0;
+  // State layout (StepArgs): value (pop, i, y, x) at i * plane_stride + pop * ps + y * pitch +
+  // x * xs from the interior origin; pitchv vertices per row.  FP32/BF16: (f, g) interleaved
+  // (xs = 2, ps = 1); FP64: planar (xs = 1, ps = 25 planes).
+  int pitchv = 0, pitch = 0, xs = 1;
   size_t plane_stride = 0;
+  ptrdiff_t ps = 0;
+  void* dense = nullptr;                 // dense staging state for host transfers (on demand)
   AxisK ax{}, ay{};
   MapK map{};
   Consts cs{};
@@ -177,6 +183,8 @@ static StepArgs step_args(sllbm_ctx* c, const void* src, void* dst) {
   a.P = c->P;
   a.nv = c->nv;
   a.plane_stride = c->plane_stride;
+  a.xs = c->xs;
+  a.ps = c->ps;
   a.offx = c->offx;
   a.offy = c->offy;
   a.wx = c->wx;
@@ -223,13 +231,13 @@ static GeomArgs geom_args(sllbm_ctx* c) {
 // taken from a cell in the middle of each axis; a vertex "follows the pattern" when its offset
 // and weights match those of its local node for all five components.  The fused kernel writes
 // only vertices that follow the pattern on both axes; the others go to the gather kernel.
-static sllbm_status axis_pattern(sllbm_ctx* c, const AxisK& ax, const int* off_dev, const float* w_dev,
+static sllbm_status axis_pattern(sllbm_ctx* c, const AxisK& ax, const int* off_dev, const double* w_dev,
                                  bool is_y, std::vector<unsigned char>& stdv, bool* ok) {
   const int n = ax.nv, P = c->P;
   std::vector<int> off((size_t)kQ1 * n);
-  std::vector<float> w((size_t)kQ1 * n * (P + 1));
+  std::vector<double> w((size_t)kQ1 * n * (P + 1));
   CUDA_TRY(c, cudaMemcpyAsync(off.data(), off_dev, off.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(w.data(), w_dev, w.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(w.data(), w_dev, w.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   *ok = ax.n_cells >= 3;
   const int jref0 = (ax.n_cells / 2) * P;
@@ -238,7 +246,7 @@ static sllbm_status axis_pattern(sllbm_ctx* c, const AxisK& ax, const int* off_d
       const int j = jref0 + k;
       const int d = off[(size_t)comp * n + j];
       if (d < -P || d > 0) { *ok = false; break; }   // taps must stay within the band [-P, P]
-      const float* wj = &w[((size_t)comp * n + j) * (P + 1)];
+      const double* wj = &w[((size_t)comp * n + j) * (P + 1)];
       if (is_y) {
         c->ut.dy_pat[comp][k] = d;
         for (int al = 0; al <= P; ++al) c->ut.wy_pat[comp][k][al] = wj[al];
@@ -252,11 +260,11 @@ static sllbm_status axis_pattern(sllbm_ctx* c, const AxisK& ax, const int* off_d
     const int k = j % P;
     for (int comp = 0; comp < kQ1; ++comp) {
       const int d = off[(size_t)comp * n + j];
-      const float* wj = &w[((size_t)comp * n + j) * (P + 1)];
+      const double* wj = &w[((size_t)comp * n + j) * (P + 1)];
       const int dref = off[(size_t)comp * n + jref0 + k];
-      const float* wr = &w[((size_t)comp * n + jref0 + k) * (P + 1)];
+      const double* wr = &w[((size_t)comp * n + jref0 + k) * (P + 1)];
       bool same = (d == dref);
-      for (int al = 0; al <= P && same; ++al) same = fabsf(wj[al] - wr[al]) <= 1e-6f;
+      for (int al = 0; al <= P && same; ++al) same = fabs(wj[al] - wr[al]) <= 1e-6;
       if (!same) stdv[j] = 0;
     }
   }
@@ -266,12 +274,11 @@ static sllbm_status axis_pattern(sllbm_ctx* c, const AxisK& ax, const int* off_d
 static sllbm_status build_uniform_pattern(sllbm_ctx* c) {
   c->ut.valid = false;
   // 16-byte staging chunks must not straddle the periodic seam, and tiles need a few cells
-  const int chunk = (c->store == kStoreBF16) ? 8 : 4;
-  if (c->ax.periodic && c->nx % chunk != 0) return SLLBM_OK;
+  if (c->xs != 2 || (c->ax.periodic && c->nx % 4 != 0)) return SLLBM_OK;
   std::vector<unsigned char> sx, sy;
   bool okx = false, oky = false;
-  TRY(axis_pattern(c, c->ax, c->offx, c->wx, false, sx, &okx));
-  TRY(axis_pattern(c, c->ay, c->offy, c->wy, true, sy, &oky));
+  TRY(axis_pattern(c, c->ax, c->offx, c->wx64, false, sx, &okx));
+  TRY(axis_pattern(c, c->ay, c->offy, c->wy64, true, sy, &oky));
   if (!okx || !oky) return SLLBM_OK;
   if (!c->std_x) {
     TRY(dalloc(c, &c->std_x, (size_t)c->nx));
@@ -300,30 +307,41 @@ static sllbm_status build_uniform_pattern(sllbm_ctx* c) {
   return SLLBM_OK;
 }
 
-static cudaError_t copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
-  // dense [npop*25][ny][nx] <-> interior of the ghost-cell layout [planes][rows_alloc][pitch]
-  cudaMemcpy3DParms m = {};
-  const size_t row = (size_t)c->nx * c->elem, prow = (size_t)c->pitch * c->elem;
-  cudaPitchedPtr dense = make_cudaPitchedPtr(nullptr, row, c->nx, c->ny);
-  cudaPitchedPtr inner = make_cudaPitchedPtr(nullptr, prow, c->pitch, c->rows_alloc);
-  if (to_internal) {
-    dense.ptr = const_cast<void*>(src);
-    inner.ptr = dst;
-    m.srcPtr = dense;
-    m.dstPtr = inner;
-  } else {
-    inner.ptr = const_cast<void*>(src);
-    dense.ptr = dst;
-    m.srcPtr = inner;
-    m.dstPtr = dense;
+// Dense [npop][25][ny][nx] <-> the internal layout.  Host transfers go through the dense staging
+// buffer (one contiguous copy) and the conversion kernel.
+static cudaError_t convert_state(sllbm_ctx* c, const void* src, void* dst, bool to_internal) {
+  return launch_state_convert(src, dst, to_internal, c->elem, c->npop, c->nx, c->ny, c->pitch,
+                              c->plane_stride, c->xs, c->ps, c->stream);
+}
+
+static size_t dense_bytes(const sllbm_ctx* c) { return (size_t)c->npop * kQ * c->nv * c->elem; }
+
+static sllbm_status copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
+  if (kind == cudaMemcpyDeviceToDevice) {
+    CUDA_TRY(c, convert_state(c, src, dst, to_internal));
+    return SLLBM_OK;
   }
-  m.extent = make_cudaExtent(row, c->ny, (size_t)c->npop * kQ);
-  m.kind = kind;
-  return cudaMemcpy3DAsync(&m, c->stream);
+  if (!c->dense) {
+    char* p = nullptr;
+    TRY(dalloc(c, &p, dense_bytes(c)));
+    c->dense = p;
+  }
+  if (to_internal) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->dense, src, dense_bytes(c), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, convert_state(c, c->dense, dst, true));
+  } else {
+    CUDA_TRY(c, convert_state(c, src, c->dense, false));
+    CUDA_TRY(c, cudaMemcpyAsync(dst, c->dense, dense_bytes(c), cudaMemcpyDeviceToHost, c->stream));
+  }
+  return SLLBM_OK;
 }
 
 static cudaError_t fill_ghosts(sllbm_ctx* c) {
   if (!c->ghost.on) return cudaSuccess;
+  // interleaved layout: an (f, g) pair moves as one element of twice the size
+  if (c->xs == 2)
+    return launch_ghost_fill(c->state[c->cur], 2 * c->elem, c->plane_stride / 2, c->pitchv, kQ,
+                             c->ghost, c->stream);
   return launch_ghost_fill(c->state[c->cur], c->elem, c->plane_stride, c->pitch, c->npop * kQ,
                            c->ghost, c->stream);
 }
@@ -401,8 +419,11 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   // and below for the last tile's halo), rows 16-byte aligned for every storage type.
   c->gxr = (c->nx + 31) / 32 * 32 - c->nx + 8;
   c->rows_alloc = c->gy + c->ny + c->gyb;
-  c->pitch = (c->gx + c->nx + c->gxr + 7) / 8 * 8;
+  c->pitchv = (c->gx + c->nx + c->gxr + 7) / 8 * 8;
+  c->xs = (c->store == kStoreF64) ? 1 : 2;
+  c->pitch = c->pitchv * c->xs;
   c->plane_stride = (size_t)c->rows_alloc * c->pitch;
+  c->ps = (c->xs == 2) ? 1 : (ptrdiff_t)kQ * c->plane_stride;
   c->ghost.on = 0;
   c->ghost.px = c->ax.periodic;
   c->ghost.py = c->ay.periodic;
@@ -413,13 +434,13 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   c->ghost.ylo = -c->gy;
   c->ghost.yhi = c->ny + c->gyb;
   sllbm_status s;
-  const size_t state_elems = (size_t)2 * kQ * c->plane_stride;
+  const size_t state_elems = (size_t)2 * kQ * c->rows_alloc * c->pitchv;
   for (int k = 0; k < 2; ++k) {
     void* ptr = nullptr;
     s = dalloc(c, reinterpret_cast<char**>(&ptr), state_elems * c->elem);
     if (s != SLLBM_OK) { sllbm_destroy(c); return s; }
     c->alloc[k] = ptr;
-    c->state[k] = static_cast<char*>(ptr) + ((size_t)c->gy * c->pitch + c->gx) * c->elem;
+    c->state[k] = static_cast<char*>(ptr) + ((size_t)c->gy * c->pitch + (size_t)c->gx * c->xs) * c->elem;
     if (cudaMemsetAsync(ptr, 0, state_elems * c->elem, c->stream) != cudaSuccess) {
       sllbm_destroy(c);
       return SLLBM_ERR_CUDA;
@@ -546,6 +567,8 @@ sllbm_status sllbm_init_equilibrium(sllbm_ctx* c, const double* rho, const doubl
   a.pitch = c->pitch;
   a.nv = c->nv;
   a.plane_stride = c->plane_stride;
+  a.xs = c->xs;
+  a.ps = c->ps;
   a.cs = c->cs;
   a.cp = c->cp;
   a.store = c->store;
@@ -599,13 +622,13 @@ int sllbm_launches_per_step(const sllbm_ctx* c) {
 
 sllbm_status sllbm_get_state(sllbm_ctx* c, void* dst) {
   if (!c || !dst) return fail(c, SLLBM_ERR_ARG, "null pointer");
-  CUDA_TRY(c, copy_state(c, dst, c->state[c->cur], false, cudaMemcpyDeviceToDevice));
+  TRY(copy_state(c, dst, c->state[c->cur], false, cudaMemcpyDeviceToDevice));
   return SLLBM_OK;
 }
 
 sllbm_status sllbm_set_state(sllbm_ctx* c, const void* src) {
   if (!c || !src) return fail(c, SLLBM_ERR_ARG, "null pointer");
-  CUDA_TRY(c, copy_state(c, c->state[c->cur], src, true, cudaMemcpyDeviceToDevice));
+  TRY(copy_state(c, c->state[c->cur], src, true, cudaMemcpyDeviceToDevice));
   CUDA_TRY(c, fill_ghosts(c));
   c->initialized = true;
   return SLLBM_OK;
@@ -614,11 +637,11 @@ sllbm_status sllbm_set_state(sllbm_ctx* c, const void* src) {
 sllbm_status sllbm_step_host(sllbm_ctx* c, const void* in, void* out, int nsteps) {
   if (!c || !in || !out || nsteps < 0) return fail(c, SLLBM_ERR_ARG, "bad arguments");
   if (!c->precomputed) return fail(c, SLLBM_ERR_STATE, "precompute_departures first");
-  CUDA_TRY(c, copy_state(c, c->state[c->cur], in, true, cudaMemcpyHostToDevice));
+  TRY(copy_state(c, c->state[c->cur], in, true, cudaMemcpyHostToDevice));
   CUDA_TRY(c, fill_ghosts(c));
   c->initialized = true;
   for (int k = 0; k < nsteps; ++k) CUDA_TRY(c, enqueue_step(c));
-  CUDA_TRY(c, copy_state(c, out, c->state[c->cur], false, cudaMemcpyDeviceToHost));
+  TRY(copy_state(c, out, c->state[c->cur], false, cudaMemcpyDeviceToHost));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return SLLBM_OK;
 }
@@ -633,6 +656,8 @@ sllbm_status sllbm_moments(sllbm_ctx* c, float* rho, float* u, float* v, float* 
   a.pitch = c->pitch;
   a.nv = c->nv;
   a.plane_stride = c->plane_stride;
+  a.xs = c->xs;
+  a.ps = c->ps;
   a.cs = c->cs;
   a.cp = c->cp;
   a.store = c->store;

@@ -17,7 +17,11 @@ struct StepArgs {
   void* dst;
   int nx, ny, pitch, periodic_x, periodic_y, P;
   long long nv;
-  size_t plane_stride;  // elements between population planes (ny * pitch)
+  // State layout: value (pop, i, y, x) at src[i * plane_stride + pop * ps + y * pitch + x * xs]
+  // (interior origin).  FP32/BF16 storage interleaves f and g (xs = 2, ps = 1); FP64 is planar.
+  size_t plane_stride;  // elements between velocity planes
+  int xs;               // elements between neighbouring vertices of a row
+  ptrdiff_t ps;         // elements between the f and g values of one (velocity, vertex)
   const int* offx;
   const int* offy;
   const float* wx;      // [5][nx][P+1]
@@ -49,8 +53,8 @@ struct StepArgs {
 struct UniformTables {
   bool valid;
   bool tall;                  // 16-row tiles (one CTA per SM) or 8-row tiles (two per SM)
-  float wy_pat[kQ1][4][5];    // [b][l][alpha]
-  float wx_pat[kQ1][4][5];    // [a][k][alpha]
+  double wy_pat[kQ1][4][5];   // [b][l][alpha]
+  double wx_pat[kQ1][4][5];   // [a][k][alpha]
   int dy_pat[kQ1][4];         // [b][l]: stencil start - vertex row, in [-p, 0]
   int dx_pat[kQ1][4];         // [a][k]: stencil start - vertex column, in [-p, 0]
   const unsigned char* std_x; // [nx]: column follows the pattern
@@ -90,11 +94,17 @@ struct InitArgs {
   int nx, ny, pitch;
   long long nv;
   size_t plane_stride;
+  int xs;
+  ptrdiff_t ps;
   Consts cs;
   CollideK cp;
   int store;
 };
 cudaError_t launch_init_equilibrium(const InitArgs& a, cudaStream_t s);
+// Dense [npop][25][ny][nx] <-> internal layout (interior origin `internal`), element size `elem`.
+cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int npop,
+                                 int nx, int ny, int pitch, size_t plane_stride, int xs,
+                                 ptrdiff_t ps, cudaStream_t s);
 // Copy the periodic images of interior vertices into the ghost cells of `planes` planes (clamped
 // copies on non-periodic axes).  `origin`: interior origin of plane 0; elem: bytes per element.
 cudaError_t launch_ghost_fill(void* origin, int elem, size_t plane_stride, int pitch, int planes,
@@ -106,6 +116,8 @@ struct MomentArgs {
   int nx, ny, pitch;
   long long nv;
   size_t plane_stride;
+  int xs;
+  ptrdiff_t ps;
   Consts cs;
   CollideK cp;
   int store;

@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const __grid_const
   double m = 0.0, en = 0.0;
   if (v < a.nv) {
     const int ix = (int)(v % a.nx), iy = (int)(v / a.nx);
-    const size_t o = (size_t)iy * a.pitch + ix;
+    const size_t o = (size_t)iy * a.pitch + (size_t)ix * a.xs;
     const int npop = a.cp.npop;
     double rho = 0.0, jx = 0.0, jy = 0.0, e2 = 0.0;
     for (int i = 0; i < kQ; ++i) {
@@ -25,15 +25,15 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const __grid_const
       if (Store == kStoreF64) {
         const double* s = static_cast<const double*>(a.src);
         fv = s[(size_t)i * a.plane_stride + o];
-        if (npop == 2) gv = s[(size_t)(kQ + i) * a.plane_stride + o];
+        if (npop == 2) gv = s[(size_t)i * a.plane_stride + a.ps + o];
       } else if (Store == kStoreF32) {
         const float* s = static_cast<const float*>(a.src);
         fv = s[(size_t)i * a.plane_stride + o];
-        if (npop == 2) gv = s[(size_t)(kQ + i) * a.plane_stride + o];
+        if (npop == 2) gv = s[(size_t)i * a.plane_stride + a.ps + o];
       } else {
         const __nv_bfloat16* s = static_cast<const __nv_bfloat16*>(a.src);
         fv = __bfloat162float(s[(size_t)i * a.plane_stride + o]);
-        if (npop == 2) gv = __bfloat162float(s[(size_t)(kQ + i) * a.plane_stride + o]);
+        if (npop == 2) gv = __bfloat162float(s[(size_t)i * a.plane_stride + a.ps + o]);
       }
       rho += fv;
       jx += fv * cx;
@@ -171,6 +171,8 @@ extern "C" sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, in
   a.pitch = nx;
   a.nv = nv;
   a.plane_stride = (size_t)nv;
+  a.xs = 1;                       // dense planar input: g planes follow the 25 f planes
+  a.ps = (ptrdiff_t)kQ * nv;
   const double s10 = sqrt(10.0), sm = sqrt(5.0 - s10), lg = sqrt(5.0 + s10);
   const double xi[5] = {0.0, sm, lg, -sm, -lg};
   for (int k = 0; k < 5; ++k) a.cs.xi[k] = xi[k];

@@ -226,7 +226,7 @@ __global__ void init_eq_kernel(const __grid_constant__ InitArgs a) {
   const double q = theta - 1.0;
   EqFactors<double> e;
   eq_factors<double>(a.cs.he, ux, uy, q, e);
-  const size_t o = (size_t)iy * a.pitch + ix;
+  const size_t o = (size_t)iy * a.pitch + (size_t)ix * a.xs;
   for (int ia = 0; ia < kQ1; ++ia)
     for (int ib = 0; ib < kQ1; ++ib) {
       const int i = 5 * ia + ib;
@@ -234,7 +234,7 @@ __global__ void init_eq_kernel(const __grid_constant__ InitArgs a) {
       const double em1 = eq_em1<double>(e, ia, ib);
       const double devf = (rho - 1.0) + rho * em1;          // f^eq / w - 1
       const double devg = devf + q * (1.0 + devf);          // g^eq / (K w) - 1
-      const size_t of = (size_t)i * a.plane_stride + o, og = (size_t)(kQ + i) * a.plane_stride + o;
+      const size_t of = (size_t)i * a.plane_stride + o, og = of + a.ps;
       if (Store == kStoreF64) {
         double* d = static_cast<double*>(a.dst);
         d[of] = w * (1.0 + devf);
@@ -314,6 +314,51 @@ cudaError_t launch_ghost_fill(void* origin, int elem, size_t plane_stride, int p
     case 2: ghost_fill_kernel<uint16_t><<<blocks, threads, 0, s>>>(static_cast<uint16_t*>(origin), plane_stride, pitch, planes, g); break;
     case 4: ghost_fill_kernel<uint32_t><<<blocks, threads, 0, s>>>(static_cast<uint32_t*>(origin), plane_stride, pitch, planes, g); break;
     case 8: ghost_fill_kernel<uint64_t><<<blocks, threads, 0, s>>>(static_cast<uint64_t*>(origin), plane_stride, pitch, planes, g); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Dense [npop][25][ny][nx] <-> internal layout (ghost cells, row pitch, interleaved pairs).
+// ------------------------------------------------------------------------------------------
+template <typename E>
+__global__ void state_convert_kernel(const E* src, E* dst, int to_internal, int npop, int nx, int ny,
+                                     int pitch, size_t plane_stride, int xs, ptrdiff_t ps) {
+  const long long nv = (long long)nx * ny;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)npop * kQ * nv) return;
+  const long long pl = t / nv, v = t - pl * nv;
+  const int pop = (int)(pl / kQ), i = (int)(pl - (long long)pop * kQ);
+  const int x = (int)(v % nx), y = (int)(v / nx);
+  const ptrdiff_t o = (ptrdiff_t)i * plane_stride + pop * ps + (ptrdiff_t)y * pitch + (ptrdiff_t)x * xs;
+  if (to_internal)
+    dst[o] = src[t];
+  else
+    dst[t] = src[o];
+}
+
+cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int npop,
+                                 int nx, int ny, int pitch, size_t plane_stride, int xs,
+                                 ptrdiff_t ps, cudaStream_t s) {
+  const long long n = (long long)npop * kQ * nx * ny;
+  if (n == 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  const int ti = to_internal ? 1 : 0;
+  switch (elem) {
+    case 2:
+      state_convert_kernel<uint16_t><<<blocks, threads, 0, s>>>(static_cast<const uint16_t*>(src),
+          static_cast<uint16_t*>(dst), ti, npop, nx, ny, pitch, plane_stride, xs, ps);
+      break;
+    case 4:
+      state_convert_kernel<uint32_t><<<blocks, threads, 0, s>>>(static_cast<const uint32_t*>(src),
+          static_cast<uint32_t*>(dst), ti, npop, nx, ny, pitch, plane_stride, xs, ps);
+      break;
+    case 8:
+      state_convert_kernel<uint64_t><<<blocks, threads, 0, s>>>(static_cast<const uint64_t*>(src),
+          static_cast<uint64_t*>(dst), ti, npop, nx, ny, pitch, plane_stride, xs, ps);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -55,6 +55,25 @@ __device__ __forceinline__ float ld_store(const __nv_bfloat16* p) {
 __device__ __forceinline__ void st_store(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st_store(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
+// (f, g) pairs of the interleaved FP32/BF16 state: the two populations of one (velocity, vertex)
+// are adjacent and travel together through the interpolation, in packed FP32x2 arithmetic.
+__device__ __forceinline__ float2 ld_pair(const float* p) {
+  return __ldg(reinterpret_cast<const float2*>(p));
+}
+__device__ __forceinline__ float2 ld_pair(const __nv_bfloat16* p) {
+  return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+}
+__device__ __forceinline__ void st_pair(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+__device__ __forceinline__ void st_pair(__nv_bfloat16* p, float2 v) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __float22bfloat162_rn(v);
+}
+__device__ __forceinline__ float2 bcast2(float a) { return make_float2(a, a); }
+// a - b, rounded once (the product b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // Ghost cells of the state layout.  A plane is stored as rows [-gy, ny + gyb) x columns
 // [-gx, nx + gxr) around the interior origin; on periodic axes the ghost cells hold the periodic
 // images of interior vertices so that rectangular tile copies never wrap.  Kernels address
@@ -202,14 +221,14 @@ __device__ __forceinline__ T eq_em1(const EqFactors<T>& e, int a, int b) {
   return s;
 }
 
-// Collision of one vertex in deviation form, FP32.  vals[0..24] = f - w (pre-collision),
-// vals[25..49] = g - K w.  On return vals hold the post-collision deviations.  Returns false if
-// the density or temperature is non-positive or non-finite.
+// Collision of one vertex in deviation form, FP32.  fg[i] = (f_i - w_i, g_i - K w_i) before
+// collision (g unused with a single population); on return fg holds the post-collision
+// deviations.  Returns false if the density or temperature is non-positive or non-finite.
 //
 // With X_k(a) = A_k(u_x) he[k][a] and S_m(b) = sum_{l=1..m} A_l(u_y) he[l][b] the equilibrium
 // deviation is f_ab^eq - w_ab = w_a w_b (drho + rho S_4(b)) + sum_k (rho w_a X_k(a)) (w_b (1 +
 // S_{4-k}(b))): after a per-vertex set-up of 45 factors, five FMAs per velocity.
-__device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], const Consts& cs,
+__device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Consts& cs,
                                                       const CollideK& cp) {
   // moments (Sec. II): rho = 1 + sum fbar, j = sum fbar xi, A2 = sum fbar |xi|^2, G = sum gbar
   float rowsum[kQ1], colsum[kQ1];
@@ -221,8 +240,8 @@ __device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], con
   for (int a = 0; a < kQ1; ++a)
 #pragma unroll
     for (int b = 0; b < kQ1; ++b) {
-      rowsum[a] += vals[5 * a + b];
-      colsum[b] += vals[5 * a + b];
+      rowsum[a] += fg[5 * a + b].x;
+      colsum[b] += fg[5 * a + b].x;
     }
   float drho = 0.f, jx = 0.f, jy = 0.f, a2 = 0.f;
 #pragma unroll
@@ -235,7 +254,7 @@ __device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], con
   float G = 0.f;
   if (cp.npop == 2) {
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) G += vals[kQ + i];
+    for (int i = 0; i < kQ; ++i) G += fg[i].y;
   }
   const float rho = 1.f + drho;
   const float inv_rho = 1.f / rho;
@@ -290,12 +309,12 @@ __device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], con
       for (int k = 1; k <= 4; ++k) ef += Xw[k - 1][a] * Sw[4 - k][b];
       erow[a] += ef;
       ecol[b] += ef;
-      vals[i] = keep * vals[i] + om * ef;
+      fg[i].x = keep * fg[i].x + om * ef;
       if (cp.npop == 2) {
         // g^eq - K w = K ((1 + q)(f^eq - w) + q w)   (g^eq = K theta f^eq, Sec. II.D)
         const float egi = Kq1 * ef + Kq * (cs.wf[a] * cs.wf[b]);
         eg += egi;
-        vals[kQ + i] = keep * vals[kQ + i] + om * egi;
+        fg[i].y = keep * fg[i].y + om * egi;
       }
     }
   // Residual moments of (equilibrium - pre-collision state); remove them with the smallest
@@ -318,8 +337,8 @@ __device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], con
     for (int b = 0; b < kQ1; ++b) {
       const int i = 5 * a + b;
       const float wb = ta * cs.wf[b];
-      vals[i] -= wb * (ca + r2 * cs.xif[b]);
-      if (cp.npop == 2) vals[kQ + i] -= wb * c3;
+      fg[i].x -= wb * (ca + r2 * cs.xif[b]);
+      if (cp.npop == 2) fg[i].y -= wb * c3;
     }
   }
   if (cp.npop != 2) {
@@ -331,7 +350,7 @@ __device__ __forceinline__ bool collide_deviation_f32(float (&vals)[2 * kQ], con
 #pragma unroll
       for (int b = 0; b < kQ1; ++b) {
         const float x2 = cs.xif[a] * cs.xif[a] + cs.xif[b] * cs.xif[b];
-        vals[5 * a + b] -= om * cs.wf[a] * cs.wf[b] * c * (x2 - 2.f);
+        fg[5 * a + b].x -= om * cs.wf[a] * cs.wf[b] * c * (x2 - 2.f);
       }
   }
   return (rho > 0.f) && (q > -1.f) && isfinite(rho) && isfinite(q);

@@ -36,14 +36,14 @@ __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_consta
     }
     double accf = 0.0, accg = 0.0;
     const double* pf = src + (size_t)i * a.plane_stride;
-    const double* pg = src + (size_t)(kQ + i) * a.plane_stride;
+    const double* pg = pf + a.ps;
 #pragma unroll
     for (int kb = 0; kb <= P; ++kb) {
       const size_t r = (size_t)wrap_index(sy + kb, a.ny, a.periodic_y) * a.pitch;
       double axf = 0.0, axg = 0.0;
 #pragma unroll
       for (int ka = 0; ka <= P; ++ka) {
-        const size_t o = r + wrap_index(sx + ka, a.nx, a.periodic_x);
+        const size_t o = r + (size_t)wrap_index(sx + ka, a.nx, a.periodic_x) * a.xs;
         axf += wx[ka] * __ldg(pf + o);
         if (npop == 2) axg += wx[ka] * __ldg(pg + o);
       }
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_consta
   EqFactors<double> e;
   eq_factors<double>(a.cs.he, ux, uy, q, e);
   const double om = a.cp.omega;
-  const size_t o = (size_t)iy * a.pitch + ix;
+  const size_t o = (size_t)iy * a.pitch + (size_t)ix * a.xs;
 #pragma unroll
   for (int ia = 0; ia < kQ1; ++ia)
 #pragma unroll
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_consta
       dst[(size_t)i * a.plane_stride + o] = f[i] - om * (f[i] - feq);
       if (npop == 2) {
         const double geq = a.cp.K * theta * feq;
-        dst[(size_t)(kQ + i) * a.plane_stride + o] = g[i] - om * (g[i] - geq);
+        dst[(size_t)i * a.plane_stride + a.ps + o] = g[i] - om * (g[i] - geq);
       }
     }
   if (!(rho > 0.0 && theta > 0.0 && isfinite(rho) && isfinite(theta))) atomicOr(a.flag, 1);

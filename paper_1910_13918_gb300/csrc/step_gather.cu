@@ -1,5 +1,7 @@
 // Generic fused SLLBM step, FP32 arithmetic: one thread per vertex gathers the (p+1)^2 stencil of
-// every velocity plane straight from global memory (L1/L2 cached), then collides.
+// every velocity plane straight from global memory (L1/L2 cached), then collides.  The state is
+// the interleaved FP32/BF16 layout: each load brings the (f, g) pair of one (velocity, vertex),
+// and both populations are interpolated together in packed FP32x2 arithmetic.
 //
 // Used for transformed grids (per-(velocity, vertex) departure descriptors, Sec. III.E) and for
 // uniform grids whose departure offsets exceed the staging halo of the fused uniform kernel.
@@ -20,7 +22,7 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
   const int ix = (int)(v % a.nx), iy = (int)(v / a.nx);
   const Store* src = static_cast<const Store*>(a.src);
   Store* dst = static_cast<Store*>(a.dst);
-  float vals[2 * kQ];
+  float2 fg[kQ];   // (f, g) deviations after streaming
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const int ia = i / 5, ib = i % 5;
@@ -45,42 +47,34 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
     long long row[P + 1];
 #pragma unroll
     for (int k = 0; k <= P; ++k) {
-      col[k] = wrap_index(sx + k, a.nx, a.periodic_x);
+      col[k] = 2 * wrap_index(sx + k, a.nx, a.periodic_x);
       row[k] = (long long)wrap_index(sy + k, a.ny, a.periodic_y) * a.pitch;
     }
+    const Store* pl = src + (size_t)i * a.plane_stride;
+    // difference form (see the uniform kernel): constants are reproduced exactly in FP32
+    float2 rows[P + 1];
 #pragma unroll
-    for (int pop = 0; pop < 2; ++pop) {
-      if (pop < a.cp.npop) {
-        const Store* pl = src + (size_t)(pop * kQ + i) * a.plane_stride;
-        // difference form (see the uniform kernel): constants are reproduced exactly in FP32
-        float rows[P + 1];
+    for (int kb = 0; kb <= P; ++kb) {
+      const float2 base = ld_pair(pl + row[kb] + col[0]);
+      float2 accx = base;
 #pragma unroll
-        for (int kb = 0; kb <= P; ++kb) {
-          const float base = ld_store(pl + row[kb] + col[0]);
-          float accx = base;
-#pragma unroll
-          for (int ka = 1; ka <= P; ++ka) accx += wx[ka] * (ld_store(pl + row[kb] + col[ka]) - base);
-          rows[kb] = accx;
-        }
-        float acc = rows[0];
-#pragma unroll
-        for (int kb = 1; kb <= P; ++kb) acc += wy[kb] * (rows[kb] - rows[0]);
-        vals[pop * kQ + i] = acc;
-      } else {
-        vals[pop * kQ + i] = 0.f;
-      }
+      for (int ka = 1; ka <= P; ++ka)
+        accx = fma2(bcast2(wx[ka]), sub2(ld_pair(pl + row[kb] + col[ka]), base), accx);
+      rows[kb] = accx;
     }
+    float2 acc = rows[0];
+#pragma unroll
+    for (int kb = 1; kb <= P; ++kb) acc = fma2(bcast2(wy[kb]), sub2(rows[kb], rows[0]), acc);
+    fg[i] = acc;
   }
-  const bool ok = collide_deviation_f32(vals, a.cs, a.cp);
+  const bool two = a.cp.npop == 2;
+  const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
   if (!ok) atomicOr(a.flag, 1);
   store_images(a.ghost, ix, iy, [&](int xx, int yy) {
-    const ptrdiff_t o = (ptrdiff_t)yy * a.pitch + xx;
+    Store* o = dst + (ptrdiff_t)yy * a.pitch + 2 * (ptrdiff_t)xx;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) st_store(dst + (ptrdiff_t)i * a.plane_stride + o, vals[i]);
-    if (a.cp.npop == 2) {
-#pragma unroll
-      for (int i = 0; i < kQ; ++i) st_store(dst + (ptrdiff_t)(kQ + i) * a.plane_stride + o, vals[kQ + i]);
-    }
+    for (int i = 0; i < kQ; ++i)
+      st_pair(o + (ptrdiff_t)i * a.plane_stride, two ? fg[i] : make_float2(fg[i].x, 0.f));
   });
 }
 

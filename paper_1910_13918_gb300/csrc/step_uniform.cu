@@ -10,15 +10,27 @@
 // zero-gradient boundaries) are not written here; the host runs the gather kernel on exactly
 // those vertices afterwards.
 //
-// Persistent CTAs (one or two per SM) walk over tiles of 32 x TY vertices (TY a multiple of p),
-// one vertex per thread.  The 50 planes of a tile are done in 5 stages, one per x component a.  A stage (the 10 planes b = 0..4 of f and g) is copied into
-// shared memory by two TMA tensor copies (tile + stencil halo; the state layout carries ghost
-// cells with the periodic images, so a tile never wraps), completing on an mbarrier, two stages
-// ahead in three buffers.  Phase k runs the y pass of stage k (task = (plane, staged column),
-// register window of the column) and the x pass of stage k-1 (thread = vertex): six barriers per
-// tile.  After stage 4 every thread holds the 50 pre-collision deviations of its vertex, collides
-// in registers and writes 50 coalesced rows (plus periodic images in the ghost cells), while the
-// first two stages of its next tile are already in flight.
+// State: f and g share the departure points, so the state interleaves them ((f, g) pairs per
+// velocity plane and vertex) and every interpolation step moves and combines the pair at once:
+// 64-bit shared-memory and global accesses, packed FP32x2 FMAs.
+//
+// Persistent CTAs (one or two per SM) walk over tiles of 32 x TY vertices (TY a multiple of 2p),
+// one vertex per thread.  The 25 pair planes of a tile are done in 5 stages, one per x component
+// a.  A stage (the 5 planes b = 0..4) is copied into shared memory by one TMA tensor copy (tile +
+// stencil halo; the state layout carries ghost cells with the periodic images, so a tile never
+// wraps), completing on an mbarrier, two stages ahead in three buffers.  Phase k runs the y pass
+// of stage k (task = plane b, staged column, half of the rows: register window of the column) and
+// the x pass of stage k-1 (thread = vertex): six barriers per tile.  After stage 4 every thread
+// holds the 50 pre-collision deviations of its vertex, collides in registers and writes 25
+// coalesced rows of pairs (plus periodic images in the ghost cells), while the first two stages
+// of its next tile are already in flight.
+//
+// Interpolation form: sum_alpha w_alpha v_{s+alpha} is evaluated as
+//   v_s + sum_{alpha >= 1} W_alpha (v_{s+alpha} - v_{s+alpha-1}),  W_alpha = sum_{beta >= alpha} w_beta,
+// equal to it because the weights sum to one.  A constant field is reproduced exactly in FP32
+// (with the FP32-rounded weights themselves the deficit of their sum would bias every uniform
+// region the same way every step, a systematic mass drift), and in the y pass the differences of
+// a staged column are formed once and shared by all the rows that read them.
 #include <cuda.h>
 
 #include "kernels.h"
@@ -27,35 +39,37 @@ namespace sllbm {
 
 namespace {
 
-// Tile of 32 x TY vertices; TY a multiple of p: the "tall" tile (16 rows, 15 for p = 3, one CTA
-// of 512 threads per SM) or the "short" one (8 rows, 6 for p = 3, two CTAs per SM).
+// Tile of 32 x TY vertices; TY a multiple of 2p: the "tall" tile (16 rows, 12 for p = 3, one CTA
+// of 32 TY threads per SM) or the "short" one (8 rows, 6 for p = 3, two CTAs per SM).  A y-pass
+// task covers RC = TY / 2 rows of one staged column, from a window of RW = RC + 2p staged rows.
 template <int P, bool Tall>
 struct TileShape {
-  static constexpr int TY = Tall ? ((P == 3) ? 15 : 16) : ((P == 3) ? 6 : 8);
+  static constexpr int TY = Tall ? ((P == 3) ? 12 : 16) : ((P == 3) ? 6 : 8);
   static constexpr int NT = 32 * TY;
   static constexpr int MINB = Tall ? 1 : 2;      // CTAs per SM
   static constexpr int R = TY + 2 * P;           // staged rows y0-P .. y0+TY-1+P
-  static constexpr int G = 10;                   // planes per stage
+  static constexpr int NH = 2;                   // row halves per staged column
+  static constexpr int RC = TY / NH;             // rows per y-pass task (a multiple of P)
+  static constexpr int RW = RC + 2 * P;          // window rows per y-pass task
+  static_assert(RC % P == 0, "row chunks must hold whole periods of the pattern");
 };
 
 constexpr int kStageBuffers = 3;   // TMA staging buffers per CTA (prefetch distance 2 stages)
+constexpr int kCO = 4;             // staged column origin x0 - 4: 16-byte aligned for both pair types
+constexpr int kC = 32 + 2 * kCO;   // staged columns
 
-template <typename Store>
-struct StoreShape {
-  static constexpr int CO = 16 / sizeof(Store);   // staged column origin x0 - CO (16-byte aligned)
-  static constexpr int C = 32 + 2 * CO;           // staged columns
-};
-
-// Elements of one TMA box (5 planes x R rows x C columns), padded to 128 bytes.
+// Elements of one TMA box (5 planes x R rows x C columns x 2 populations), padded to 128 bytes.
 template <int P, bool Tall, typename Store>
 struct BoxShape {
-  static constexpr int ELEMS = 5 * TileShape<P, Tall>::R * StoreShape<Store>::C;
+  static constexpr int ELEMS = 5 * TileShape<P, Tall>::R * kC * 2;
   static constexpr int BYTES = ELEMS * (int)sizeof(Store);
   static constexpr int STRIDE = ((BYTES + 127) / 128) * 128 / (int)sizeof(Store);
 };
 
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float2 lds_pair(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 lds_pair(const __nv_bfloat16* p) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -95,63 +109,63 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
-// y interpolation of one staged column for the rows r = l (mod p), stencil start D relative to
-// the row: t[r] = sum_alpha w[alpha] * win[r + P + D + alpha]  (window row j is tile row j - P),
-// evaluated as win[s] + sum_{alpha >= 1} w[alpha] (win[s + alpha] - win[s]).  Since the weights
-// sum to one the two are equal, but the second reproduces a constant field exactly in FP32:
-// FP32-rounded weights do not sum to one exactly, and in the first form the deficit would bias
-// every uniform region the same way every step (a systematic mass drift).
-template <int P, int TY, int R, int D>
-__device__ __forceinline__ void y_taps(const float (&win)[R], const float (&w)[P + 1], int l,
-                                       float* tout, int C) {
+// y interpolation of the rows rr = l (mod p) of a task, stencil start D relative to the row:
+// window row j is task row j - P, so the stencil of row rr starts at window row s = rr + P + D.
+template <int P, int RC, int RW, int D>
+__device__ __forceinline__ void y_taps(const float2 (&win)[RW], const float2 (&dl)[RW - 1],
+                                       const float2 (&W)[P + 1], int l, float2* tout) {
 #pragma unroll
-  for (int r = 0; r < TY; ++r) {
-    if (r % P != l) continue;
-    const float base = win[r + P + D];
-    float acc = base;
+  for (int rr = 0; rr < RC; ++rr) {
+    if (rr % P != l) continue;
+    const int s = rr + P + D;
+    float2 acc = win[s];
 #pragma unroll
-    for (int al = 1; al <= P; ++al) acc += w[al] * (win[r + P + D + al] - base);
-    tout[r * C] = acc;
+    for (int al = 1; al <= P; ++al) acc = fma2(W[al], dl[s + al - 1], acc);
+    tout[rr * kC] = acc;
   }
 }
 
-// y pass of one stage: task = (plane g, staged column c) with exact taps of (b, l).  The first
-// G*32 tasks give each warp one plane (warp-uniform b, no divergence in the tap switch); the
-// remaining G*(C-32) cover the right-hand staged columns.  Kept out of line: the same code
-// serves the five stages of a tile, which keeps the instruction footprint small.
-template <int P, int TY, int R, int G, int C, int NT, typename Store>
-__device__ __noinline__ void y_pass(const Store* Sst, int box_stride, float* Tst, const float* WY,
-                                    const int* DY, int npop) {
+// y pass of one stage: task = (plane b, row half h, staged column c).  The first 5*NH*32 tasks
+// give each warp one (b, h) (warp-uniform tap switch, no divergence); the remaining 5*NH*(C-32)
+// cover the right-hand staged columns.  Kept out of line: the same code serves the five stages
+// of a tile, which keeps the instruction footprint small.
+template <int P, bool Tall, typename Store>
+__device__ __noinline__ void y_pass(const Store* Sst, float2* Tst, const float* WY, const int* DY) {
+  using TS = TileShape<P, Tall>;
+  constexpr int TY = TS::TY, R = TS::R, NH = TS::NH, RC = TS::RC, RW = TS::RW, NT = TS::NT;
   const int tid = threadIdx.x;
 #pragma unroll 1
-  for (int t = tid; t < G * C; t += NT) {
+  for (int t = tid; t < kQ1 * NH * kC; t += NT) {
     int g, c;
-    if (t < G * 32) {
+    if (t < kQ1 * NH * 32) {
       g = t >> 5;
       c = t & 31;
     } else {
-      g = (t - G * 32) / (C - 32);
-      c = 32 + (t - G * 32) - g * (C - 32);
+      const int u = t - kQ1 * NH * 32;
+      g = u / (kC - 32);
+      c = 32 + u - g * (kC - 32);
     }
-    const int pop = g >= 5, b = g - 5 * pop;
-    if (pop >= npop) continue;
-    const Store* col = Sst + (size_t)pop * box_stride + (size_t)b * R * C + c;
-    float win[R];
+    const int b = g / NH, h = g - b * NH;
+    const Store* col = Sst + ((size_t)(b * R + h * RC) * kC + c) * 2;
+    float2 win[RW], dl[RW - 1];
 #pragma unroll
-    for (int j = 0; j < R; ++j) win[j] = to_f(col[j * C]);
-    float* tout = Tst + (size_t)g * TY * C + c;
+    for (int j = 0; j < RW; ++j) win[j] = lds_pair(col + j * kC * 2);
+#pragma unroll
+    for (int j = 0; j < RW - 1; ++j) dl[j] = sub2(win[j + 1], win[j]);
+    float2* tout = Tst + ((size_t)b * TY + h * RC) * kC + c;
 #pragma unroll
     for (int l = 0; l < P; ++l) {
-      float w[P + 1];
+      float2 W[P + 1];
       const float* wp = WY + (b * P + l) * 8;
+      W[0] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int al = 0; al <= P; ++al) w[al] = wp[al];
+      for (int al = 1; al <= P; ++al) W[al] = bcast2(wp[al]);
       switch (DY[b * P + l]) {
-        case 0: y_taps<P, TY, R, 0>(win, w, l, tout, C); break;
-        case -1: y_taps<P, TY, R, -1>(win, w, l, tout, C); break;
-        case -2: if constexpr (P >= 2) y_taps<P, TY, R, -2>(win, w, l, tout, C); break;
-        case -3: if constexpr (P >= 3) y_taps<P, TY, R, -3>(win, w, l, tout, C); break;
-        case -4: if constexpr (P >= 4) y_taps<P, TY, R, -4>(win, w, l, tout, C); break;
+        case 0: y_taps<P, RC, RW, 0>(win, dl, W, l, tout); break;
+        case -1: y_taps<P, RC, RW, -1>(win, dl, W, l, tout); break;
+        case -2: if constexpr (P >= 2) y_taps<P, RC, RW, -2>(win, dl, W, l, tout); break;
+        case -3: if constexpr (P >= 3) y_taps<P, RC, RW, -3>(win, dl, W, l, tout); break;
+        case -4: if constexpr (P >= 4) y_taps<P, RC, RW, -4>(win, dl, W, l, tout); break;
         default: break;
       }
     }
@@ -162,15 +176,15 @@ __device__ __noinline__ void y_pass(const Store* Sst, int box_stride, float* Tst
 
 template <int P>
 struct UniformPattern {
-  float wy[kQ1][P][8];                   // y taps: P+1 weights per (b, l)
-  float wx[kQ1][P][8];                   // x taps: P+1 weights per (a, k)
+  float wy[kQ1][P][8];                   // y taps: tail sums W_1..W_P per (b, l) at [1..P]
+  float wx[kQ1][P][8];                   // x taps: tail sums W_1..W_P per (a, k) at [1..P]
   int dy[kQ1][P];                        // y stencil start relative to the row, in [-P, 0]
   int dx[kQ1][P];                        // x stencil start relative to the column, in [-P, 0]
 };
 
-template <int P, typename Store>
+template <int P>
 struct UniformArgs {
-  CUtensorMap tmap;                      // 3D map of the source state: (column, row, plane)
+  CUtensorMap tmap;                      // 3D map of the source state: (pair element, row, plane)
   StepArgs a;
   UniformPattern<P> pat;
   const unsigned char* std_x;            // [nx] 1 if the column follows the pattern
@@ -180,29 +194,26 @@ struct UniformArgs {
 
 template <int P, typename Store, bool Tall>
 __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MINB)
-    step_uniform_kernel(const __grid_constant__ UniformArgs<P, Store> ua) {
+    step_uniform_kernel(const __grid_constant__ UniformArgs<P> ua) {
   using TS = TileShape<P, Tall>;
-  using SS = StoreShape<Store>;
   using BS = BoxShape<P, Tall, Store>;
-  constexpr int TY = TS::TY, NT = TS::NT, R = TS::R, G = TS::G;
-  constexpr int C = SS::C, CO = SS::CO;
+  constexpr int TY = TS::TY, NT = TS::NT;
   constexpr int NSB = kStageBuffers;   // stage k lands in S[k % NSB], issued NSB-1 stages ahead
   constexpr int PD = NSB - 1;
   const StepArgs& a = ua.a;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem_raw = smem_dyn + ((128 - (smem_u32(smem_dyn) & 127)) & 127);
-  Store* S = reinterpret_cast<Store*>(smem_raw);                       // [3][2][box]
-  float* T = reinterpret_cast<float*>(S + NSB * 2 * BS::STRIDE);       // [2][G][TY][C]
-  float* WX = T + 2 * G * TY * C;                                     // [5][P][8]
-  float* WY = WX + kQ1 * P * 8;                                       // [5][P][8]
-  int* DX = reinterpret_cast<int*>(WY + kQ1 * P * 8);                 // [5][P]
-  int* DY = DX + kQ1 * P;                                             // [5][P]
-  uint64_t* BAR = reinterpret_cast<uint64_t*>(DY + kQ1 * P);         // [NSB], 8-byte aligned
+  Store* S = reinterpret_cast<Store*>(smem_raw);                        // [NSB][box]
+  float2* T = reinterpret_cast<float2*>(S + NSB * BS::STRIDE);         // [2][5][TY][C]
+  float* WX = reinterpret_cast<float*>(T + 2 * kQ1 * TY * kC);         // [5][P][8]
+  float* WY = WX + kQ1 * P * 8;                                        // [5][P][8]
+  int* DX = reinterpret_cast<int*>(WY + kQ1 * P * 8);                  // [5][P]
+  int* DY = DX + kQ1 * P;                                              // [5][P]
+  uint64_t* BAR = reinterpret_cast<uint64_t*>(DY + kQ1 * P);          // [NSB], 8-byte aligned
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, row = tid >> 5;
-  const int npop = a.cp.npop;
-  const unsigned stage_bytes = (unsigned)(npop * BS::BYTES);
+  const bool two = a.cp.npop == 2;
   const int tiles_x = (a.nx + 31) / 32;
   const int ntiles = tiles_x * ((a.ny + TY - 1) / TY);
 
@@ -221,17 +232,16 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   __syncthreads();  // tables and barriers
 
   // Global stage counter: the k-th tile of this CTA has stages 5k .. 5k+4; stage s lands in
-  // S[s % 3] and completes phase (s / 3) & 1 of BAR[s % 3]; it is issued two stages ahead, so the
-  // first two stages of the next tile are in flight while a tile finishes and collides.
+  // S[s % NSB] and completes phase (s / NSB) & 1 of BAR[s % NSB]; it is issued PD stages ahead, so
+  // the first stages of the next tile are in flight while a tile finishes and collides.
   auto issue = [&](int tile, int st, long s) {
     if (tid == 0 && tile < ntiles) {
       const int buf = (int)(s % NSB);
       const int tx0 = (tile % tiles_x) * 32, ty0 = (tile / tiles_x) * TY;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      mbar_expect_tx(&BAR[buf], stage_bytes);
-      for (int pop = 0; pop < npop; ++pop)
-        tma_load_3d(S + (size_t)(buf * 2 + pop) * BS::STRIDE, &ua.tmap, ua.gx + tx0 - CO,
-                    ua.gy + ty0 - P, pop * kQ + 5 * st, &BAR[buf]);
+      mbar_expect_tx(&BAR[buf], (unsigned)BS::BYTES);
+      tma_load_3d(S + (size_t)buf * BS::STRIDE, &ua.tmap, 2 * (ua.gx + tx0 - kCO), ua.gy + ty0 - P,
+                  5 * st, &BAR[buf]);
     }
   };
 
@@ -242,55 +252,53 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s0 += kQ1) {
     const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * TY;
     const int x = x0 + lane, y = y0 + row;
-    float vals[2 * kQ];
+    float2 fg[kQ];   // (f, g) after streaming, velocity i = 5a + b
 #pragma unroll
     for (int ph = 0; ph <= kQ1; ++ph) {
       const long s = s0 + ph;
       if (ph < kQ1) mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);  // stage landed
-      __syncthreads();  // T[(s-1)&1] written; T[s&1] and S[(s+2)%3] no longer read
+      __syncthreads();  // T[(s-1)&1] written; T[s&1] and S[(s+PD)%NSB] no longer read
       if (ph + PD < kQ1)
         issue(tile, ph + PD, s + PD);
       else if (ph < kQ1)
         issue(tile + gridDim.x, ph + PD - kQ1, s + PD);   // the next tile's first stages
       if (ph < kQ1)
-        y_pass<P, TY, R, G, C, NT, Store>(S + (size_t)(s % NSB) * 2 * BS::STRIDE, BS::STRIDE,
-                                          T + (size_t)(s & 1) * G * TY * C, WY, DY, npop);
+        y_pass<P, Tall, Store>(S + (size_t)(s % NSB) * BS::STRIDE, T + (size_t)(s & 1) * kQ1 * TY * kC,
+                               WY, DY);
 
       // ---- x pass of stage ph-1: thread = vertex; exact taps of (a, k = x mod p) ----
       if (ph >= 1) {
         const int st = ph - 1;
         const int k = x % P;
         const float* w = WX + (st * P + k) * 8;
-        const int cbase = lane + CO + DX[st * P + k];
-        float wr[P + 1];
+        const int cbase = lane + kCO + DX[st * P + k];
+        float2 W[P + 1];
 #pragma unroll
-        for (int al = 0; al <= P; ++al) wr[al] = w[al];
+        for (int al = 1; al <= P; ++al) W[al] = bcast2(w[al]);
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          const int pop = g / 5, b = g % 5;
-          const float* trow = T + (((size_t)((s - 1) & 1) * G + g) * TY + row) * C + cbase;
-          const float base = trow[0];   // difference form, as in y_taps
-          float acc = base;
+        for (int b = 0; b < kQ1; ++b) {
+          const float2* trow = T + (((size_t)((s - 1) & 1) * kQ1 + b) * TY + row) * kC + cbase;
+          float2 prev = trow[0], acc = prev;
 #pragma unroll
-          for (int al = 1; al <= P; ++al) acc += wr[al] * (trow[al] - base);
-          vals[pop * kQ + 5 * st + b] = (pop < npop) ? acc : 0.f;
+          for (int al = 1; al <= P; ++al) {
+            const float2 cur = trow[al];
+            acc = fma2(W[al], sub2(cur, prev), acc);
+            prev = cur;
+          }
+          fg[5 * st + b] = acc;
         }
       }
     }
 
-    const bool ok = collide_deviation_f32(vals, a.cs, a.cp);
+    const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
     if (x < a.nx && y < a.ny && ua.std_x[x] && ua.std_y[y]) {
       if (!ok) atomicOr(a.flag, 1);
       Store* dst = static_cast<Store*>(a.dst);
       store_images(a.ghost, x, y, [&](int xx, int yy) {
-        const ptrdiff_t o = (ptrdiff_t)yy * a.pitch + xx;
+        Store* o = dst + (ptrdiff_t)yy * a.pitch + 2 * (ptrdiff_t)xx;
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) st_store(dst + (ptrdiff_t)i * a.plane_stride + o, vals[i]);
-        if (npop == 2) {
-#pragma unroll
-          for (int i = 0; i < kQ; ++i)
-            st_store(dst + (ptrdiff_t)(kQ + i) * a.plane_stride + o, vals[kQ + i]);
-        }
+        for (int i = 0; i < kQ; ++i)
+          st_pair(o + (ptrdiff_t)i * a.plane_stride, two ? fg[i] : make_float2(fg[i].x, 0.f));
       });
     }
   }
@@ -302,10 +310,9 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
 template <int P, typename Store, bool Tall>
 static size_t smem_bytes() {
   using TS = TileShape<P, Tall>;
-  using SS = StoreShape<Store>;
   using BS = BoxShape<P, Tall, Store>;
-  return 128 + sizeof(Store) * kStageBuffers * 2 * BS::STRIDE + sizeof(float) * 2 * TS::G * TS::TY * SS::C +
-         sizeof(float) * 2 * kQ1 * P * 8 + sizeof(int) * (2 * kQ1 * P + 2) + sizeof(uint64_t) * kStageBuffers;
+  return 128 + sizeof(Store) * kStageBuffers * BS::STRIDE + sizeof(float2) * 2 * kQ1 * TS::TY * kC +
+         sizeof(float) * 2 * kQ1 * P * 8 + sizeof(int) * 2 * kQ1 * P + sizeof(uint64_t) * kStageBuffers;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -329,15 +336,21 @@ static EncodeTiledFn encode_fn() {
 template <int P, typename Store, bool Tall>
 static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStream_t s) {
   using TS = TileShape<P, Tall>;
-  using SS = StoreShape<Store>;
-  UniformArgs<P, Store> ua;
+  if (a.xs != 2 || a.ps != 1) return cudaErrorNotSupported;   // interleaved (f, g) pairs only
+  UniformArgs<P> ua;
   memset(&ua, 0, sizeof(ua));
   ua.a = a;
   for (int c = 0; c < kQ1; ++c)
     for (int l = 0; l < P; ++l) {
-      for (int j = 0; j < 8; ++j) {
-        ua.pat.wx[c][l][j] = j <= P ? t.wx_pat[c][l][j] : 0.f;
-        ua.pat.wy[c][l][j] = j <= P ? t.wy_pat[c][l][j] : 0.f;
+      // tail sums W_alpha = sum_{beta >= alpha} w_beta, from the FP64 weights
+      for (int j = 1; j <= P; ++j) {
+        double tx = 0.0, ty = 0.0;
+        for (int m = j; m <= P; ++m) {
+          tx += t.wx_pat[c][l][m];
+          ty += t.wy_pat[c][l][m];
+        }
+        ua.pat.wx[c][l][j] = (float)tx;
+        ua.pat.wy[c][l][j] = (float)ty;
       }
       ua.pat.dx[c][l] = t.dx_pat[c][l];
       ua.pat.dy[c][l] = t.dy_pat[c][l];
@@ -346,15 +359,15 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
   ua.std_y = t.std_y;
   ua.gx = t.gx;
   ua.gy = t.gy;
-  // tensor map over the whole source allocation (ghost cells included)
+  // tensor map over the whole source allocation (ghost cells included), pairs as 2 elements
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   const char* base = static_cast<const char*>(a.src) -
-                     ((ptrdiff_t)t.gy * a.pitch + t.gx) * (ptrdiff_t)sizeof(Store);
-  const cuuint64_t dims[3] = {(cuuint64_t)a.pitch, (cuuint64_t)t.rows_alloc, (cuuint64_t)(2 * kQ)};
+                     ((ptrdiff_t)t.gy * a.pitch + 2 * (ptrdiff_t)t.gx) * (ptrdiff_t)sizeof(Store);
+  const cuuint64_t dims[3] = {(cuuint64_t)a.pitch, (cuuint64_t)t.rows_alloc, (cuuint64_t)kQ};
   const cuuint64_t strides[2] = {(cuuint64_t)a.pitch * sizeof(Store),
                                  (cuuint64_t)a.plane_stride * sizeof(Store)};
-  const cuuint32_t box[3] = {(cuuint32_t)SS::C, (cuuint32_t)TS::R, 5u};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * kC), (cuuint32_t)TS::R, 5u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = enc(&ua.tmap, sizeof(Store) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                    3, const_cast<char*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -404,7 +417,7 @@ cudaError_t launch_step_uniform(const StepArgs& a, const UniformTables& t, int s
 }
 
 int uniform_tile_rows(int P, bool tall) {
-  return tall ? (P == 3 ? 15 : 16) : (P == 3 ? 6 : 8);
+  return tall ? (P == 3 ? 12 : 16) : (P == 3 ? 6 : 8);
 }
 
 }  // namespace sllbm
