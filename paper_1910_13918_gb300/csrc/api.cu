@@ -280,6 +280,13 @@ static sllbm_status build_uniform_pattern(sllbm_ctx* c) {
   TRY(axis_pattern(c, c->ax, c->offx, c->wx64, false, sx, &okx));
   TRY(axis_pattern(c, c->ay, c->offy, c->wy64, true, sy, &oky));
   if (!okx || !oky) return SLLBM_OK;
+  // The fused kernel's y pass takes each stencil as a whole cell: start offset -l at local node
+  // l, or -P at node 0 (a departure into the cell before).  Anything else goes to the gather path.
+  for (int comp = 0; comp < kQ1; ++comp)
+    for (int k = 0; k < c->P; ++k) {
+      const int d = c->ut.dy_pat[comp][k];
+      if (k == 0 ? (d != 0 && d != -c->P) : d != -k) return SLLBM_OK;
+    }
   if (!c->std_x) {
     TRY(dalloc(c, &c->std_x, (size_t)c->nx));
     TRY(dalloc(c, &c->std_y, (size_t)c->ny));

@@ -293,12 +293,16 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
   // the equilibrium has the moments of the pre-collision state; in FP32 its fourth-order
   // polynomial carries rounding of the size of its largest terms, which would leak into the
   // conserved moments every step.
-  float erow[kQ1], ecol[kQ1], eg = 0.f;
+  float erow[kQ1], ecol[kQ1], eg = 0.f, KqW[kQ1];
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
     erow[a] = 0.f;
     ecol[a] = 0.f;
+    KqW[a] = Kq * cs.wf[a];
   }
+  // The g lanes are computed whatever the population count (with one population they hold
+  // zeros and are never stored); f and g relax together in packed FP32x2 arithmetic.
+  const float2 keep2 = bcast2(keep), om2 = bcast2(om);
 #pragma unroll
   for (int a = 0; a < kQ1; ++a)
 #pragma unroll
@@ -309,18 +313,15 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
       for (int k = 1; k <= 4; ++k) ef += Xw[k - 1][a] * Sw[4 - k][b];
       erow[a] += ef;
       ecol[b] += ef;
-      fg[i].x = keep * fg[i].x + om * ef;
-      if (cp.npop == 2) {
-        // g^eq - K w = K ((1 + q)(f^eq - w) + q w)   (g^eq = K theta f^eq, Sec. II.D)
-        const float egi = Kq1 * ef + Kq * (cs.wf[a] * cs.wf[b]);
-        eg += egi;
-        fg[i].y = keep * fg[i].y + om * egi;
-      }
+      // g^eq - K w = K ((1 + q)(f^eq - w) + q w)   (g^eq = K theta f^eq, Sec. II.D)
+      const float egi = Kq1 * ef + cs.wf[a] * KqW[b];
+      eg += egi;
+      fg[i] = fma2(keep2, fg[i], __fmul2_rn(om2, make_float2(ef, egi)));
     }
   // Residual moments of (equilibrium - pre-collision state); remove them with the smallest
   // correction in the span of w {1, xi_x, xi_y} (mass, momentum) and w on g (energy).  This
   // changes nothing in exact arithmetic and restores conservation to the rounding of the sums.
-  float r0 = -drho, r1 = -jx, r2 = -jy, r3 = -(a2 + G) + eg;
+  float r0 = -drho, r1 = -jx, r2 = -jy, r3 = -(a2 + G) + (cp.npop == 2 ? eg : 0.f);
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
     r0 += erow[a];
@@ -329,6 +330,13 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
     r3 += cs.xif[a] * cs.xif[a] * (erow[a] + ecol[a]);
   }
   const float c3 = r3 - 2.f * r0;   // energy residual left after the mass correction
+  // per b: w_b r2 xi_b and w_b c3, so that each velocity takes three FMAs
+  float r2w[kQ1], c3w[kQ1];
+#pragma unroll
+  for (int b = 0; b < kQ1; ++b) {
+    r2w[b] = r2 * (cs.wf[b] * cs.xif[b]);
+    c3w[b] = c3 * cs.wf[b];
+  }
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
     const float ta = om * cs.wf[a];
@@ -336,9 +344,9 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
 #pragma unroll
     for (int b = 0; b < kQ1; ++b) {
       const int i = 5 * a + b;
-      const float wb = ta * cs.wf[b];
-      fg[i].x -= wb * (ca + r2 * cs.xif[b]);
-      if (cp.npop == 2) fg[i].y -= wb * c3;
+      // om w_a w_b (r0 + r1 xi_a + r2 xi_b) on f, om w_a w_b c3 on g
+      fg[i].x -= ta * (ca * cs.wf[b] + r2w[b]);
+      fg[i].y -= ta * c3w[b];
     }
   }
   if (cp.npop != 2) {

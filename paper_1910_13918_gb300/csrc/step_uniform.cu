@@ -18,11 +18,11 @@
 // one vertex per thread.  The 25 pair planes of a tile are done in 5 stages, one per x component
 // a.  A stage (the 5 planes b = 0..4) is copied into shared memory by one TMA tensor copy (tile +
 // stencil halo; the state layout carries ghost cells with the periodic images, so a tile never
-// wraps), completing on an mbarrier, two stages ahead in three buffers.  Phase k runs the y pass
+// wraps), completing on an mbarrier, three stages ahead in four buffers.  Phase k runs the y pass
 // of stage k (task = plane b, staged column, half of the rows: register window of the column) and
 // the x pass of stage k-1 (thread = vertex): six barriers per tile.  After stage 4 every thread
 // holds the 50 pre-collision deviations of its vertex, collides in registers and writes 25
-// coalesced rows of pairs (plus periodic images in the ghost cells), while the first two stages
+// coalesced rows of pairs (plus periodic images in the ghost cells), while the first stages
 // of its next tile are already in flight.
 //
 // Interpolation form: sum_alpha w_alpha v_{s+alpha} is evaluated as
@@ -39,24 +39,38 @@ namespace sllbm {
 
 namespace {
 
+// Stencils of the pattern.  The stencil of a departure point is the cell that contains it, so it
+// starts on a cell boundary; with the offset D in [-p, 0] of the start relative to the vertex this
+// leaves, for the vertex at local node l of its cell, D = -l (own cell) or, at l = 0 only,
+// D = -p (the cell before).  (The host checks the tables for exactly this form.)  Staged rows
+// therefore reach from y0 - p (D = -p at the tile's first row) to y0 + TY (the last cell of the
+// tile), and the start row of every stencil is a cell boundary.
+//
 // Tile of 32 x TY vertices; TY a multiple of 2p: the "tall" tile (16 rows, 12 for p = 3, one CTA
 // of 32 TY threads per SM) or the "short" one (8 rows, 6 for p = 3, two CTAs per SM).  A y-pass
-// task covers RC = TY / 2 rows of one staged column, from a window of RW = RC + 2p staged rows.
+// task covers RC = TY / 2 rows of one staged column, from a window of RW = RC + p + 1 rows.
 template <int P, bool Tall>
 struct TileShape {
   static constexpr int TY = Tall ? ((P == 3) ? 12 : 16) : ((P == 3) ? 6 : 8);
   static constexpr int NT = 32 * TY;
   static constexpr int MINB = Tall ? 1 : 2;      // CTAs per SM
-  static constexpr int R = TY + 2 * P;           // staged rows y0-P .. y0+TY-1+P
+  static constexpr int R = TY + P + 1;           // staged rows y0-P .. y0+TY
   static constexpr int NH = 2;                   // row halves per staged column
   static constexpr int RC = TY / NH;             // rows per y-pass task (a multiple of P)
-  static constexpr int RW = RC + 2 * P;          // window rows per y-pass task
+  static constexpr int RW = RC + P + 1;          // window rows per y-pass task
   static_assert(RC % P == 0, "row chunks must hold whole periods of the pattern");
 };
 
-constexpr int kStageBuffers = 3;   // TMA staging buffers per CTA (prefetch distance 2 stages)
+constexpr int kStageBuffers = 4;   // TMA staging buffers per CTA (prefetch distance 3 stages)
 constexpr int kCO = 4;             // staged column origin x0 - 4: 16-byte aligned for both pair types
 constexpr int kC = 32 + 2 * kCO;   // staged columns
+// Rows of the y-pass output T keep column c at c + c / 16: a gap every 16 columns spreads the
+// cell-aligned reads of the x pass (lanes of one cell read the same columns, cells 4 columns
+// apart) over all shared-memory banks.
+constexpr int kTC = kC + kC / 16;  // T row length (pairs)
+__host__ __device__ constexpr int tpos(int c) { return c + (c >> 4); }
+// ints of the DX [5][P] and EY [5] tables, rounded up to keep the mbarriers 8-byte aligned
+__host__ __device__ constexpr int table_ints(int P) { return (kQ1 * P + kQ1 + 1) / 2 * 2; }
 
 // Elements of one TMA box (5 planes x R rows x C columns x 2 populations), padded to 128 bytes.
 template <int P, bool Tall, typename Store>
@@ -109,66 +123,67 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
       : "memory");
 }
 
-// y interpolation of the rows rr = l (mod p) of a task, stencil start D relative to the row:
-// window row j is task row j - P, so the stencil of row rr starts at window row s = rr + P + D.
-template <int P, int RC, int RW, int D>
-__device__ __forceinline__ void y_taps(const float2 (&win)[RW], const float2 (&dl)[RW - 1],
-                                       const float2 (&W)[P + 1], int l, float2* tout) {
+// y interpolation of the RC rows of a task.  Window row j is task row j - P; row rr = m p + l
+// has its stencil in cell m + e of the window (rows (m + e) p .. (m + e + 1) p), e = 1 except
+// at l = 0 when the plane's departures fall in the cell before (E0 = false).  Straight-line code:
+// the RC outputs are independent and interleave freely.
+template <int P, int RC, int RW, bool E0>
+__device__ __forceinline__ void y_rows(const float2 (&win)[RW], const float2 (&dl)[RW - 1],
+                                       const float2 (&W)[P][P], float2* __restrict__ tout) {
 #pragma unroll
   for (int rr = 0; rr < RC; ++rr) {
-    if (rr % P != l) continue;
-    const int s = rr + P + D;
+    const int l = rr % P, m = rr / P;
+    const int s = (m + ((l == 0 && !E0) ? 0 : 1)) * P;
     float2 acc = win[s];
 #pragma unroll
-    for (int al = 1; al <= P; ++al) acc = fma2(W[al], dl[s + al - 1], acc);
-    tout[rr * kC] = acc;
+    for (int al = 1; al <= P; ++al) acc = fma2(W[l][al - 1], dl[s + al - 1], acc);
+    tout[rr * kTC] = acc;
   }
 }
 
 // y pass of one stage: task = (plane b, row half h, staged column c).  The first 5*NH*32 tasks
-// give each warp one (b, h) (warp-uniform tap switch, no divergence); the remaining 5*NH*(C-32)
-// cover the right-hand staged columns.  Kept out of line: the same code serves the five stages
-// of a tile, which keeps the instruction footprint small.
+// give each warp one (b, h) and 32 columns; the right-hand C-32 columns of the NH halves of a
+// plane b go to one more warp per b (NH*(C-32) of its lanes).  Every warp thus has one b, and the
+// branch on the plane's cell choice never diverges.
 template <int P, bool Tall, typename Store>
-__device__ __noinline__ void y_pass(const Store* Sst, float2* Tst, const float* WY, const int* DY) {
+__device__ __forceinline__ void y_pass(const Store* __restrict__ Sst, float2* __restrict__ Tst,
+                                    const float2* __restrict__ WY, const int* __restrict__ EY) {
   using TS = TileShape<P, Tall>;
   constexpr int TY = TS::TY, R = TS::R, NH = TS::NH, RC = TS::RC, RW = TS::RW, NT = TS::NT;
+  constexpr int CR = kC - 32;
+  static_assert(NH * CR <= 32, "right-hand columns of one plane must fit in a warp");
   const int tid = threadIdx.x;
 #pragma unroll 1
-  for (int t = tid; t < kQ1 * NH * kC; t += NT) {
-    int g, c;
+  for (int t = tid; t < kQ1 * (NH + 1) * 32; t += NT) {
+    int b, h, c;
     if (t < kQ1 * NH * 32) {
-      g = t >> 5;
+      const int g = t >> 5;
+      b = g / NH;
+      h = g - b * NH;
       c = t & 31;
     } else {
-      const int u = t - kQ1 * NH * 32;
-      g = u / (kC - 32);
-      c = 32 + u - g * (kC - 32);
+      const int u = t - kQ1 * NH * 32, lane = u & 31;
+      if (lane >= NH * CR) continue;
+      b = u >> 5;
+      h = lane / CR;
+      c = 32 + lane - h * CR;
     }
-    const int b = g / NH, h = g - b * NH;
     const Store* col = Sst + ((size_t)(b * R + h * RC) * kC + c) * 2;
     float2 win[RW], dl[RW - 1];
 #pragma unroll
     for (int j = 0; j < RW; ++j) win[j] = lds_pair(col + j * kC * 2);
 #pragma unroll
     for (int j = 0; j < RW - 1; ++j) dl[j] = sub2(win[j + 1], win[j]);
-    float2* tout = Tst + ((size_t)b * TY + h * RC) * kC + c;
+    float2* tout = Tst + ((size_t)b * TY + h * RC) * kTC + tpos(c);
+    float2 W[P][P];   // tail sums of the plane's P row classes, in registers
 #pragma unroll
-    for (int l = 0; l < P; ++l) {
-      float2 W[P + 1];
-      const float* wp = WY + (b * P + l) * 8;
-      W[0] = make_float2(0.f, 0.f);
+    for (int l = 0; l < P; ++l)
 #pragma unroll
-      for (int al = 1; al <= P; ++al) W[al] = bcast2(wp[al]);
-      switch (DY[b * P + l]) {
-        case 0: y_taps<P, RC, RW, 0>(win, dl, W, l, tout); break;
-        case -1: y_taps<P, RC, RW, -1>(win, dl, W, l, tout); break;
-        case -2: if constexpr (P >= 2) y_taps<P, RC, RW, -2>(win, dl, W, l, tout); break;
-        case -3: if constexpr (P >= 3) y_taps<P, RC, RW, -3>(win, dl, W, l, tout); break;
-        case -4: if constexpr (P >= 4) y_taps<P, RC, RW, -4>(win, dl, W, l, tout); break;
-        default: break;
-      }
-    }
+      for (int al = 0; al < P; ++al) W[l][al] = WY[(b * P + l) * 4 + al];
+    if (EY[b])
+      y_rows<P, RC, RW, true>(win, dl, W, tout);
+    else
+      y_rows<P, RC, RW, false>(win, dl, W, tout);
   }
 }
 
@@ -178,7 +193,7 @@ template <int P>
 struct UniformPattern {
   float wy[kQ1][P][8];                   // y taps: tail sums W_1..W_P per (b, l) at [1..P]
   float wx[kQ1][P][8];                   // x taps: tail sums W_1..W_P per (a, k) at [1..P]
-  int dy[kQ1][P];                        // y stencil start relative to the row, in [-P, 0]
+  int ey[kQ1];                           // y: 1 if D(b, 0) = 0, 0 if D(b, 0) = -P
   int dx[kQ1][P];                        // x stencil start relative to the column, in [-P, 0]
 };
 
@@ -204,12 +219,12 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem_raw = smem_dyn + ((128 - (smem_u32(smem_dyn) & 127)) & 127);
   Store* S = reinterpret_cast<Store*>(smem_raw);                        // [NSB][box]
-  float2* T = reinterpret_cast<float2*>(S + NSB * BS::STRIDE);         // [2][5][TY][C]
-  float* WX = reinterpret_cast<float*>(T + 2 * kQ1 * TY * kC);         // [5][P][8]
-  float* WY = WX + kQ1 * P * 8;                                        // [5][P][8]
-  int* DX = reinterpret_cast<int*>(WY + kQ1 * P * 8);                  // [5][P]
-  int* DY = DX + kQ1 * P;                                              // [5][P]
-  uint64_t* BAR = reinterpret_cast<uint64_t*>(DY + kQ1 * P);          // [NSB], 8-byte aligned
+  float2* T = reinterpret_cast<float2*>(S + NSB * BS::STRIDE);         // [2][5][TY][kTC]
+  float2* WX = T + 2 * kQ1 * TY * kTC;                                 // [5][P][4]: (W, W)
+  float2* WY = WX + kQ1 * P * 4;                                       // [5][P][4]
+  int* DX = reinterpret_cast<int*>(WY + kQ1 * P * 4);                  // [5][P]
+  int* EY = DX + kQ1 * P;                                              // [5]
+  uint64_t* BAR = reinterpret_cast<uint64_t*>(DX + table_ints(P));    // [NSB], 8-byte aligned
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, row = tid >> 5;
@@ -217,14 +232,13 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   const int tiles_x = (a.nx + 31) / 32;
   const int ntiles = tiles_x * ((a.ny + TY - 1) / TY);
 
-  for (int e = tid; e < kQ1 * P * 8; e += NT) {
-    (&WX[0])[e] = (&ua.pat.wx[0][0][0])[e];
-    (&WY[0])[e] = (&ua.pat.wy[0][0][0])[e];
+  for (int e = tid; e < kQ1 * P * 4; e += NT) {   // tail sums, duplicated for the (f, g) lanes
+    const int cl = e >> 2, al = (e & 3) + 1;
+    WX[e] = bcast2((&ua.pat.wx[0][0][0])[cl * 8 + al]);
+    WY[e] = bcast2((&ua.pat.wy[0][0][0])[cl * 8 + al]);
   }
-  for (int e = tid; e < kQ1 * P; e += NT) {
-    (&DX[0])[e] = (&ua.pat.dx[0][0])[e];
-    (&DY[0])[e] = (&ua.pat.dy[0][0])[e];
-  }
+  for (int e = tid; e < kQ1 * P; e += NT) (&DX[0])[e] = (&ua.pat.dx[0][0])[e];
+  if (tid < kQ1) EY[tid] = ua.pat.ey[tid];
   if (tid == 0) {
     for (int k = 0; k < NSB; ++k) mbar_init(&BAR[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -263,25 +277,30 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
       else if (ph < kQ1)
         issue(tile + gridDim.x, ph + PD - kQ1, s + PD);   // the next tile's first stages
       if (ph < kQ1)
-        y_pass<P, Tall, Store>(S + (size_t)(s % NSB) * BS::STRIDE, T + (size_t)(s & 1) * kQ1 * TY * kC,
-                               WY, DY);
+        y_pass<P, Tall, Store>(S + (size_t)(s % NSB) * BS::STRIDE, T + (size_t)(s & 1) * kQ1 * TY * kTC,
+                               WY, EY);
 
       // ---- x pass of stage ph-1: thread = vertex; exact taps of (a, k = x mod p) ----
       if (ph >= 1) {
         const int st = ph - 1;
         const int k = x % P;
-        const float* w = WX + (st * P + k) * 8;
+        const float2* w = WX + (st * P + k) * 4;
         const int cbase = lane + kCO + DX[st * P + k];
         float2 W[P + 1];
+        int tp[P + 1];   // T positions of the stencil columns
 #pragma unroll
-        for (int al = 1; al <= P; ++al) W[al] = bcast2(w[al]);
+        for (int al = 0; al <= P; ++al) {
+          if (al) W[al] = w[al - 1];
+          tp[al] = tpos(cbase + al);
+        }
+        const float2* trow0 = T + ((size_t)((s - 1) & 1) * kQ1 * TY + row) * kTC;
 #pragma unroll
         for (int b = 0; b < kQ1; ++b) {
-          const float2* trow = T + (((size_t)((s - 1) & 1) * kQ1 + b) * TY + row) * kC + cbase;
-          float2 prev = trow[0], acc = prev;
+          const float2* trow = trow0 + b * TY * kTC;
+          float2 prev = trow[tp[0]], acc = prev;
 #pragma unroll
           for (int al = 1; al <= P; ++al) {
-            const float2 cur = trow[al];
+            const float2 cur = trow[tp[al]];
             acc = fma2(W[al], sub2(cur, prev), acc);
             prev = cur;
           }
@@ -311,8 +330,8 @@ template <int P, typename Store, bool Tall>
 static size_t smem_bytes() {
   using TS = TileShape<P, Tall>;
   using BS = BoxShape<P, Tall, Store>;
-  return 128 + sizeof(Store) * kStageBuffers * BS::STRIDE + sizeof(float2) * 2 * kQ1 * TS::TY * kC +
-         sizeof(float) * 2 * kQ1 * P * 8 + sizeof(int) * 2 * kQ1 * P + sizeof(uint64_t) * kStageBuffers;
+  return 128 + sizeof(Store) * kStageBuffers * BS::STRIDE + sizeof(float2) * 2 * kQ1 * TS::TY * kTC +
+         sizeof(float2) * 2 * kQ1 * P * 4 + sizeof(int) * table_ints(P) + sizeof(uint64_t) * kStageBuffers;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -340,7 +359,7 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
   UniformArgs<P> ua;
   memset(&ua, 0, sizeof(ua));
   ua.a = a;
-  for (int c = 0; c < kQ1; ++c)
+  for (int c = 0; c < kQ1; ++c) {
     for (int l = 0; l < P; ++l) {
       // tail sums W_alpha = sum_{beta >= alpha} w_beta, from the FP64 weights
       for (int j = 1; j <= P; ++j) {
@@ -353,8 +372,12 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
         ua.pat.wy[c][l][j] = (float)ty;
       }
       ua.pat.dx[c][l] = t.dx_pat[c][l];
-      ua.pat.dy[c][l] = t.dy_pat[c][l];
+      // y stencils: D = -l, or D in {0, -P} at l = 0 (checked when the tables were built)
+      if (l == 0 ? (t.dy_pat[c][0] != 0 && t.dy_pat[c][0] != -P) : t.dy_pat[c][l] != -l)
+        return cudaErrorNotSupported;
     }
+    ua.pat.ey[c] = t.dy_pat[c][0] == 0 ? 1 : 0;
+  }
   ua.std_x = t.std_x;
   ua.std_y = t.std_y;
   ua.gx = t.gx;
