@@ -278,6 +278,10 @@ def run_ours(args):
     if rank == 0:
         peaks, src = _peaks()
         bytes_per_update = {"f32": 8, "bf16": 4, "f64": 16}[args.prec]
+        if s.kernel_name == "mapped_fused":
+            # + the departure record of each (velocity, vertex): stencil origin and (r, s), 12 B,
+            # shared by f and g: 6 B per update
+            bytes_per_update += 6
         alg_bytes = updates * bytes_per_update
         achieved = alg_bytes / (ms_step * 1e-3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))

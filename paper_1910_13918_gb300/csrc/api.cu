@@ -15,7 +15,7 @@
 
 using namespace sllbm;
 
-enum StepKernel { kKernelUniform = 0, kKernelGather = 1, kKernelPlainF64 = 2 };
+enum StepKernel { kKernelUniform = 0, kKernelGather = 1, kKernelPlainF64 = 2, kKernelMapped = 3 };
 
 struct sllbm_ctx {
   sllbm_grid_desc g;
@@ -48,8 +48,13 @@ struct sllbm_ctx {
   int offx_lo = 0, offx_hi = 0, offy_lo = 0, offy_hi = 0;
   UniformTables ut{};
   unsigned char *std_x = nullptr, *std_y = nullptr;
-  int* fix_list = nullptr;       // vertices the fused uniform kernel leaves to the gather kernel
+  int* fix_list = nullptr;       // vertices the fused kernels leave to the gather kernel
   long long n_fix = 0;
+  // mapped-grid tiles
+  MappedTables mt{};
+  int* mlc = nullptr;
+  int2* morg = nullptr;
+  unsigned char* mok = nullptr;
   // per-(velocity, vertex) descriptors
   int *dcx = nullptr, *dcy = nullptr;
   float *dr = nullptr, *ds = nullptr;
@@ -306,11 +311,149 @@ static sllbm_status build_uniform_pattern(sllbm_ctx* c) {
   c->ut.std_y = c->std_y;
   // tile height: 8-row tiles (two CTAs per SM) unless SLLBM_UNIFORM_TILE=16 asks for 16-row ones
   const char* tile = getenv("SLLBM_UNIFORM_TILE");
-  c->ut.tall = !(tile && atoi(tile) == 8);
+  c->ut.tall = tile && atoi(tile) == 16;
   c->ut.gx = c->gx;
   c->ut.gy = c->gy;
   c->ut.rows_alloc = c->rows_alloc;
   c->ut.valid = true;
+  return SLLBM_OK;
+}
+
+// Tail-weight polynomials of the Lagrange basis on the axis nodes: W_alpha(r) = sum_{beta >= alpha}
+// psi_beta(r), expanded in t = r - 1/2 (FP64 expansion, FP32 coefficients).
+static void tail_weight_polys(const double* nodes, int P, float wc[4][5]) {
+  for (int al = 0; al < 4; ++al)
+    for (int j = 0; j < 5; ++j) wc[al][j] = 0.f;
+  double tails[5][5] = {};
+  for (int b = 0; b <= P; ++b) {
+    double poly[5] = {1.0, 0, 0, 0, 0};   // coefficients in t, low order first
+    int deg = 0;
+    for (int m = 0; m <= P; ++m) {
+      if (m == b) continue;
+      const double c0 = -(nodes[m] - 0.5), inv = 1.0 / (nodes[b] - nodes[m]);
+      double next[5] = {0, 0, 0, 0, 0};
+      for (int j = 0; j <= deg; ++j) {
+        next[j + 1] += poly[j] * inv;
+        next[j] += poly[j] * c0 * inv;
+      }
+      ++deg;
+      for (int j = 0; j < 5; ++j) poly[j] = next[j];
+    }
+    for (int al = 1; al <= b; ++al)
+      for (int j = 0; j <= P; ++j) tails[al][j] += poly[j];
+  }
+  for (int al = 1; al <= P; ++al)
+    for (int j = 0; j <= P; ++j) wc[al - 1][j] = (float)tails[al][j];
+}
+
+// Staged windows of the fused mapped-grid kernel (read by step_mapped.cu).  Per tile of 32 x 8
+// vertices and velocity plane: the bounding box of the stencils (cell start nodes, unwrapped
+// across periodic seams relative to the vertex), its origin rounded down to a 16-byte boundary.
+// The window size is the largest box over all tiles; a tile whose stencils leave the ghost-cell
+// layout, or whose box exceeds the window limit, goes to the gather kernel.
+static sllbm_status build_mapped_tiles(sllbm_ctx* c) {
+  c->mt.valid = false;
+  if (c->xs != 2) return SLLBM_OK;
+  const int P = c->P, nx = c->nx, ny = c->ny;
+  const long long nv = c->nv;
+  const size_t n = (size_t)kQ * nv;
+  std::vector<int> cx(n), cy(n);
+  CUDA_TRY(c, cudaMemcpyAsync(cx.data(), c->dcx, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(cy.data(), c->dcy, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const int tiles_x = (nx + kMappedTileX - 1) / kMappedTileX, tiles_y = (ny + kMappedTileY - 1) / kMappedTileY;
+  const int ntiles = tiles_x * tiles_y;
+  const int A = (c->store == kStoreBF16) ? 4 : 2;      // pairs per 16 bytes
+  auto unwrap = [](int node, int vert, int nvert, bool periodic) {
+    if (periodic) {
+      if (node - vert > nvert / 2) node -= nvert;
+      if (node - vert < -nvert / 2) node += nvert;
+    }
+    return node;
+  };
+  const int xlo = -c->gx, xhi = nx + c->gxr, ylo = -c->gy, yhi = ny + c->gyb;
+  std::vector<int2> org((size_t)ntiles * kQ);
+  std::vector<int> extx((size_t)ntiles * kQ), exty((size_t)ntiles * kQ);
+  std::vector<unsigned char> ok(ntiles, 1);
+  int bw = 0, bh = 0;
+  for (int t = 0; t < ntiles; ++t) {
+    const int x0 = (t % tiles_x) * kMappedTileX, y0 = (t / tiles_x) * kMappedTileY;
+    for (int i = 0; i < kQ; ++i) {
+      int mnx = 1 << 30, mxx = -(1 << 30), mny = 1 << 30, mxy = -(1 << 30);
+      for (int y = y0; y < std::min(y0 + kMappedTileY, ny); ++y)
+        for (int x = x0; x < std::min(x0 + kMappedTileX, nx); ++x) {
+          const size_t d = (size_t)i * nv + (size_t)y * nx + x;
+          const int X = unwrap(cx[d] * P, x, nx, c->ax.periodic), Y = unwrap(cy[d] * P, y, ny, c->ay.periodic);
+          mnx = std::min(mnx, X);
+          mxx = std::max(mxx, X);
+          mny = std::min(mny, Y);
+          mxy = std::max(mxy, Y);
+        }
+      if (mnx < xlo || mxx + P >= xhi || mny < ylo || mxy + P >= yhi) ok[t] = 0;
+      const int ox = mnx - (((mnx + c->gx) % A) + A) % A;
+      org[(size_t)t * kQ + i] = make_int2(ox, mny);
+      extx[(size_t)t * kQ + i] = mxx + P + 1 - ox;
+      exty[(size_t)t * kQ + i] = mxy + P + 1 - mny;
+      if (ok[t]) {
+        bw = std::max(bw, extx[(size_t)t * kQ + i]);
+        bh = std::max(bh, exty[(size_t)t * kQ + i]);
+      }
+    }
+  }
+  bw = (bw + A - 1) / A * A;
+  // two CTAs per SM: at most ~110 KB of windows per CTA; a tile that needs more goes to the
+  // gather kernel
+  const size_t limit = 110 * 1024;
+  while (bw > A && mapped_smem_bytes(bw, bh, c->store) > limit) {
+    if (bw >= 2 * bh) bw -= A; else --bh;
+  }
+  if (bw < P + 1 || bh < P + 1 || 2 * bw > 256 || bh > 256) return SLLBM_OK;
+  for (int t = 0; t < ntiles; ++t)
+    for (int i = 0; i < kQ && ok[t]; ++i)
+      if (extx[(size_t)t * kQ + i] > bw || exty[(size_t)t * kQ + i] > bh) ok[t] = 0;
+  std::vector<int> lc(n, 0), fix;
+  for (int t = 0; t < ntiles; ++t) {
+    const int x0 = (t % tiles_x) * kMappedTileX, y0 = (t / tiles_x) * kMappedTileY;
+    for (int y = y0; y < std::min(y0 + kMappedTileY, ny); ++y)
+      for (int x = x0; x < std::min(x0 + kMappedTileX, nx); ++x) {
+        if (!ok[t]) {
+          fix.push_back(y * nx + x);
+          continue;
+        }
+        for (int i = 0; i < kQ; ++i) {
+          const size_t d = (size_t)i * nv + (size_t)y * nx + x;
+          const int2 o = org[(size_t)t * kQ + i];
+          const int X = unwrap(cx[d] * P, x, nx, c->ax.periodic), Y = unwrap(cy[d] * P, y, ny, c->ay.periodic);
+          lc[d] = ((Y - o.y) << 16) | (X - o.x);
+        }
+      }
+  }
+  if (fix.size() == (size_t)nv) return SLLBM_OK;   // nothing for the fused kernel
+  if (!c->mlc) {
+    TRY(dalloc(c, &c->mlc, n));
+    TRY(dalloc(c, &c->morg, org.size()));
+    TRY(dalloc(c, &c->mok, (size_t)ntiles));
+  }
+  CUDA_TRY(c, cudaMemcpy(c->mlc, lc.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->morg, org.data(), org.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->mok, ok.data(), ok.size(), cudaMemcpyHostToDevice));
+  c->n_fix = (long long)fix.size();
+  if (!fix.empty()) {
+    TRY(dalloc(c, &c->fix_list, fix.size()));
+    CUDA_TRY(c, cudaMemcpy(c->fix_list, fix.data(), fix.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  c->mt.lc = c->mlc;
+  c->mt.r = c->dr;
+  c->mt.s = c->ds;
+  c->mt.org = c->morg;
+  c->mt.tile_ok = c->mok;
+  c->mt.bw = bw;
+  c->mt.bh = bh;
+  c->mt.gx = c->gx;
+  c->mt.gy = c->gy;
+  c->mt.rows_alloc = c->rows_alloc;
+  tail_weight_polys(c->ax.nodes, P, c->mt.wc);
+  c->mt.valid = true;
   return SLLBM_OK;
 }
 
@@ -423,8 +566,15 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   c->store = p->prec == SLLBM_PREC_F32 ? kStoreF32 : (p->prec == SLLBM_PREC_BF16_STORE ? kStoreBF16 : kStoreF64);
   c->elem = c->store == kStoreF32 ? 4 : (c->store == kStoreBF16 ? 2 : 8);
   // Plane layout: ghost cells around the interior (8 columns left, 4 rows above, enough right
-  // and below for the last tile's halo), rows 16-byte aligned for every storage type.
-  c->gxr = (c->nx + 31) / 32 * 32 - c->nx + 8;
+  // and below for the last tile's halo), rows 16-byte aligned for every storage type.  Mapped
+  // grids get 16 on every side: their staged windows follow the departure displacement, which
+  // may reach a few vertex spacings across a periodic seam.
+  if (g->map != SLLBM_MAP_IDENTITY) {
+    c->gx = 16;
+    c->gy = 16;
+    c->gyb = 24;
+  }
+  c->gxr = (c->nx + 31) / 32 * 32 - c->nx + c->gx;
   c->rows_alloc = c->gy + c->ny + c->gyb;
   c->pitchv = (c->gx + c->nx + c->gxr + 7) / 8 * 8;
   c->xs = (c->store == kStoreF64) ? 1 : 2;
@@ -524,12 +674,12 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
     c->offy_lo = *std::min_element(oy.begin(), oy.end());
     c->offy_hi = *std::max_element(oy.begin(), oy.end()) + c->P;
   }
+  c->n_fix = 0;
   if (c->store == kStoreF64) {
     c->kernel = kKernelPlainF64;
   } else if (!mapped) {
     TRY(build_uniform_pattern(c));
     c->kernel = c->ut.valid ? kKernelUniform : kKernelGather;
-    c->ghost.on = (c->kernel == kKernelUniform) && (c->ax.periodic || c->ay.periodic);
   } else {
     c->kernel = kKernelGather;
   }
@@ -546,6 +696,11 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
     }
     CUDA_TRY(c, launch_descriptors(g, c->dcx, c->dcy, c->dr, c->ds, c->dr64, c->ds64, c->stream));
   }
+  if (mapped && c->store != kStoreF64) {
+    TRY(build_mapped_tiles(c));
+    if (c->mt.valid) c->kernel = kKernelMapped;
+  }
+  c->ghost.on = (c->kernel == kKernelUniform || c->kernel == kKernelMapped) && (c->ax.periodic || c->ay.periodic);
   double glx[8], glw[8];
   const int ngl = c->P + 3;
   gauss_legendre01(ngl, glx, glw);
@@ -598,6 +753,15 @@ static cudaError_t enqueue_step(sllbm_ctx* c) {
         e = launch_step_gather(a, c->store, c->stream);
       }
       break;
+    case kKernelMapped:
+      e = launch_step_mapped(a, c->mt, c->store, c->stream);
+      if (e == cudaSuccess && c->n_fix > 0) {  // tiles whose windows did not fit
+        a.vlist = c->fix_list;
+        a.nlist = c->n_fix;
+        a.mapped = 1;
+        e = launch_step_gather(a, c->store, c->stream);
+      }
+      break;
     case kKernelPlainF64: e = launch_step_plain_f64(a, c->stream); break;
     default: e = launch_step_gather(a, c->store, c->stream); break;
   }
@@ -617,13 +781,14 @@ const char* sllbm_step_kernel_name(const sllbm_ctx* c) {
   switch (c->kernel) {
     case kKernelUniform: return "uniform_fused";
     case kKernelPlainF64: return "plain_f64";
+    case kKernelMapped: return "mapped_fused";
     default: return "gather";
   }
 }
 
 int sllbm_launches_per_step(const sllbm_ctx* c) {
   if (!c) return 0;
-  return (c->kernel == kKernelUniform && c->n_fix > 0) ? 2 : 1;
+  return ((c->kernel == kKernelUniform || c->kernel == kKernelMapped) && c->n_fix > 0) ? 2 : 1;
 }
 
 

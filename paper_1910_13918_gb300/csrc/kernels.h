@@ -62,6 +62,24 @@ struct UniformTables {
   int gx, gy, rows_alloc;     // ghost columns/rows before the interior origin; rows per plane
 };
 
+// Fused shared-memory step for mapped grids: per (tile of kMappedTileX x kMappedTileY vertices,
+// velocity plane) one staged window of the source plane; writes only vertices of tiles marked in
+// tile_ok.  cudaErrorNotSupported if the tables are not valid.
+constexpr int kMappedTileX = 32, kMappedTileY = 8;
+struct MappedTables {
+  bool valid;
+  const int* lc;              // [25][nv]: (ly << 16) | lx, stencil origin inside the window
+  const float* r;             // [25][nv]: local departure coordinates in the cell
+  const float* s;
+  const int2* org;            // [ntiles][25]: window origin (node column, node row)
+  const unsigned char* tile_ok;
+  int bw, bh;                 // window: bw vertices x bh rows
+  int gx, gy, rows_alloc;     // ghost columns/rows before the interior origin; rows per plane
+  float wc[4][5];             // W_alpha(t) = sum_j wc[alpha-1][j] t^j, t = r - 1/2
+};
+cudaError_t launch_step_mapped(const StepArgs& a, const MappedTables& t, int store, cudaStream_t s);
+size_t mapped_smem_bytes(int bw, int bh, int store);
+
 // Generic FP32 gather step (one thread per vertex, (p+1)^2 gathers per plane from L1/L2).
 cudaError_t launch_step_gather(const StepArgs& a, int store, cudaStream_t s);
 // Fused shared-memory step for uniform grids (pattern band interpolation); writes only the

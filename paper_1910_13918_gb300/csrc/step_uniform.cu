@@ -14,12 +14,12 @@
 // velocity plane and vertex) and every interpolation step moves and combines the pair at once:
 // 64-bit shared-memory and global accesses, packed FP32x2 FMAs.
 //
-// Persistent CTAs (one or two per SM) walk over tiles of 32 x TY vertices (TY a multiple of 2p),
-// one vertex per thread.  The 25 pair planes of a tile are done in 5 stages, one per x component
+// Persistent CTAs (two per SM by default, or one with the tall tile) walk over tiles of 32 x TY
+// vertices (TY a multiple of p), one vertex per thread.  The 25 pair planes of a tile are done in 5 stages, one per x component
 // a.  A stage (the 5 planes b = 0..4) is copied into shared memory by one TMA tensor copy (tile +
 // stencil halo; the state layout carries ghost cells with the periodic images, so a tile never
 // wraps), completing on an mbarrier, three stages ahead in four buffers.  Phase k runs the y pass
-// of stage k (task = plane b, staged column, half of the rows: register window of the column) and
+// of stage k (task = plane b, staged column, chunk of rows: register window of the column) and
 // the x pass of stage k-1 (thread = vertex): six barriers per tile.  After stage 4 every thread
 // holds the 50 pre-collision deviations of its vertex, collides in registers and writes 25
 // coalesced rows of pairs (plus periodic images in the ghost cells), while the first stages
@@ -31,9 +31,8 @@
 // (with the FP32-rounded weights themselves the deficit of their sum would bias every uniform
 // region the same way every step, a systematic mass drift), and in the y pass the differences of
 // a staged column are formed once and shared by all the rows that read them.
-#include <cuda.h>
-
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace sllbm {
 
@@ -46,16 +45,18 @@ namespace {
 // therefore reach from y0 - p (D = -p at the tile's first row) to y0 + TY (the last cell of the
 // tile), and the start row of every stencil is a cell boundary.
 //
-// Tile of 32 x TY vertices; TY a multiple of 2p: the "tall" tile (16 rows, 12 for p = 3, one CTA
-// of 32 TY threads per SM) or the "short" one (8 rows, 6 for p = 3, two CTAs per SM).  A y-pass
-// task covers RC = TY / 2 rows of one staged column, from a window of RW = RC + p + 1 rows.
+// Tile of 32 x TY vertices: the "short" tile (8 rows, 6 for p = 3, two CTAs of 32 TY threads per
+// SM; the default: one CTA's barriers and collision burst overlap the other's interpolation) or
+// the "tall" one (16 rows, 12 for p = 3, one CTA per SM).  A y-pass task covers RC = TY / NH rows
+// of one staged column (the whole column, or half of it in the tall tile), from a window of
+// RW = RC + p + 1 rows.
 template <int P, bool Tall>
 struct TileShape {
   static constexpr int TY = Tall ? ((P == 3) ? 12 : 16) : ((P == 3) ? 6 : 8);
   static constexpr int NT = 32 * TY;
   static constexpr int MINB = Tall ? 1 : 2;      // CTAs per SM
   static constexpr int R = TY + P + 1;           // staged rows y0-P .. y0+TY
-  static constexpr int NH = 2;                   // row halves per staged column
+  static constexpr int NH = Tall ? 2 : 1;        // row chunks per staged column
   static constexpr int RC = TY / NH;             // rows per y-pass task (a multiple of P)
   static constexpr int RW = RC + P + 1;          // window rows per y-pass task
   static_assert(RC % P == 0, "row chunks must hold whole periods of the pattern");
@@ -80,49 +81,6 @@ struct BoxShape {
   static constexpr int STRIDE = ((BYTES + 127) / 128) * 128 / (int)sizeof(Store);
 };
 
-__device__ __forceinline__ float2 lds_pair(const float* p) { return *reinterpret_cast<const float2*>(p); }
-__device__ __forceinline__ float2 lds_pair(const __nv_bfloat16* p) {
-  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
-}
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for a phase of an mbarrier with an iteration limit; on timeout set bit 2 of *flag and
-// return (the results of the CTA are then garbage, but nothing hangs).
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* flag) {
-  for (long it = 0; it < (1L << 22); ++it)
-    if (mbar_try_wait(bar, parity)) return;
-  atomicOr(flag, 4);
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
 // y interpolation of the RC rows of a task.  Window row j is task row j - P; row rr = m p + l
 // has its stencil in cell m + e of the window (rows (m + e) p .. (m + e + 1) p), e = 1 except
 // at l = 0 when the plane's departures fall in the cell before (E0 = false).  Straight-line code:
@@ -141,10 +99,10 @@ __device__ __forceinline__ void y_rows(const float2 (&win)[RW], const float2 (&d
   }
 }
 
-// y pass of one stage: task = (plane b, row half h, staged column c).  The first 5*NH*32 tasks
-// give each warp one (b, h) and 32 columns; the right-hand C-32 columns of the NH halves of a
-// plane b go to one more warp per b (NH*(C-32) of its lanes).  Every warp thus has one b, and the
-// branch on the plane's cell choice never diverges.
+// y pass of one stage: task = (plane b, row chunk h, staged column c).  The first 5*NH*32 tasks
+// give each warp one (b, h) and 32 columns; the right-hand C-32 columns of the NH chunks of a
+// plane b go to one more warp per b (NH*(C-32) of its lanes) when the block has the warps, so
+// that the branch on the plane's cell choice never diverges; otherwise they are packed.
 template <int P, bool Tall, typename Store>
 __device__ __forceinline__ void y_pass(const Store* __restrict__ Sst, float2* __restrict__ Tst,
                                     const float2* __restrict__ WY, const int* __restrict__ EY) {
@@ -152,21 +110,30 @@ __device__ __forceinline__ void y_pass(const Store* __restrict__ Sst, float2* __
   constexpr int TY = TS::TY, R = TS::R, NH = TS::NH, RC = TS::RC, RW = TS::RW, NT = TS::NT;
   constexpr int CR = kC - 32;
   static_assert(NH * CR <= 32, "right-hand columns of one plane must fit in a warp");
+  // right-hand columns: one warp per plane b if the block has the warps, else packed
+  constexpr bool kSpread = kQ1 * (NH + 1) * 32 <= NT;
+  constexpr int kTasks = kSpread ? kQ1 * (NH + 1) * 32 : kQ1 * NH * (32 + CR);
   const int tid = threadIdx.x;
 #pragma unroll 1
-  for (int t = tid; t < kQ1 * (NH + 1) * 32; t += NT) {
+  for (int t = tid; t < kTasks; t += NT) {
     int b, h, c;
     if (t < kQ1 * NH * 32) {
       const int g = t >> 5;
       b = g / NH;
       h = g - b * NH;
       c = t & 31;
-    } else {
+    } else if (kSpread) {
       const int u = t - kQ1 * NH * 32, lane = u & 31;
       if (lane >= NH * CR) continue;
       b = u >> 5;
       h = lane / CR;
       c = 32 + lane - h * CR;
+    } else {
+      const int u = t - kQ1 * NH * 32;
+      b = u / (NH * CR);
+      const int r = u - b * NH * CR;
+      h = r / CR;
+      c = 32 + r - h * CR;
     }
     const Store* col = Sst + ((size_t)(b * R + h * RC) * kC + c) * 2;
     float2 win[RW], dl[RW - 1];
@@ -334,24 +301,6 @@ static size_t smem_bytes() {
          sizeof(float2) * 2 * kQ1 * P * 4 + sizeof(int) * table_ints(P) + sizeof(uint64_t) * kStageBuffers;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
-                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                  CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
-}
-
 template <int P, typename Store, bool Tall>
 static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStream_t s) {
   using TS = TileShape<P, Tall>;
@@ -402,6 +351,9 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, Tall>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)   // all of the unified L1/shared storage as shared memory
+      e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, Tall>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     configured = true;
   }
