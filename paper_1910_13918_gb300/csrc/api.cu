@@ -52,7 +52,7 @@ struct sllbm_ctx {
   long long n_fix = 0;
   // mapped-grid tiles
   MappedTables mt{};
-  int* mlc = nullptr;
+  uint32_t* mrec = nullptr;
   int2* morg = nullptr;
   unsigned char* mok = nullptr;
   // per-(velocity, vertex) descriptors
@@ -358,8 +358,11 @@ static sllbm_status build_mapped_tiles(sllbm_ctx* c) {
   const long long nv = c->nv;
   const size_t n = (size_t)kQ * nv;
   std::vector<int> cx(n), cy(n);
+  std::vector<float> rr(n), ss(n);
   CUDA_TRY(c, cudaMemcpyAsync(cx.data(), c->dcx, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(cy.data(), c->dcy, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(rr.data(), c->dr, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(ss.data(), c->ds, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   const int tiles_x = (nx + kMappedTileX - 1) / kMappedTileX, tiles_y = (ny + kMappedTileY - 1) / kMappedTileY;
   const int ntiles = tiles_x * tiles_y;
@@ -401,7 +404,7 @@ static sllbm_status build_mapped_tiles(sllbm_ctx* c) {
     }
   }
   bw = (bw + A - 1) / A * A;
-  // two CTAs per SM: at most ~110 KB of windows per CTA; a tile that needs more goes to the
+  // two CTAs per SM: at most ~110 KB of staging per CTA; a tile that needs more goes to the
   // gather kernel
   const size_t limit = 110 * 1024;
   while (bw > A && mapped_smem_bytes(bw, bh, c->store) > limit) {
@@ -411,7 +414,11 @@ static sllbm_status build_mapped_tiles(sllbm_ctx* c) {
   for (int t = 0; t < ntiles; ++t)
     for (int i = 0; i < kQ && ok[t]; ++i)
       if (extx[(size_t)t * kQ + i] > bw || exty[(size_t)t * kQ + i] > bh) ok[t] = 0;
-  std::vector<int> lc(n, 0), fix;
+  // records [field][plane][row][column]: rows up to the last tile, columns up to dpitch
+  const int dpitch = tiles_x * kMappedTileX, drows = tiles_y * kMappedTileY;
+  const size_t fstride = (size_t)kQ * drows * dpitch;
+  std::vector<uint32_t> rec(3 * fstride, 0u);
+  std::vector<int> fix;
   for (int t = 0; t < ntiles; ++t) {
     const int x0 = (t % tiles_x) * kMappedTileX, y0 = (t / tiles_x) * kMappedTileY;
     for (int y = y0; y < std::min(y0 + kMappedTileY, ny); ++y)
@@ -424,17 +431,20 @@ static sllbm_status build_mapped_tiles(sllbm_ctx* c) {
           const size_t d = (size_t)i * nv + (size_t)y * nx + x;
           const int2 o = org[(size_t)t * kQ + i];
           const int X = unwrap(cx[d] * P, x, nx, c->ax.periodic), Y = unwrap(cy[d] * P, y, ny, c->ay.periodic);
-          lc[d] = ((Y - o.y) << 16) | (X - o.x);
+          const size_t e = ((size_t)i * drows + y) * dpitch + x;
+          rec[e] = ((uint32_t)(Y - o.y) << 16) | (uint32_t)(X - o.x);
+          memcpy(&rec[fstride + e], &rr[d], 4);
+          memcpy(&rec[2 * fstride + e], &ss[d], 4);
         }
       }
   }
   if (fix.size() == (size_t)nv) return SLLBM_OK;   // nothing for the fused kernel
-  if (!c->mlc) {
-    TRY(dalloc(c, &c->mlc, n));
+  if (!c->mrec) {
+    TRY(dalloc(c, &c->mrec, rec.size()));
     TRY(dalloc(c, &c->morg, org.size()));
     TRY(dalloc(c, &c->mok, (size_t)ntiles));
   }
-  CUDA_TRY(c, cudaMemcpy(c->mlc, lc.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(c->mrec, rec.data(), rec.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->morg, org.data(), org.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(c->mok, ok.data(), ok.size(), cudaMemcpyHostToDevice));
   c->n_fix = (long long)fix.size();
@@ -442,9 +452,8 @@ static sllbm_status build_mapped_tiles(sllbm_ctx* c) {
     TRY(dalloc(c, &c->fix_list, fix.size()));
     CUDA_TRY(c, cudaMemcpy(c->fix_list, fix.data(), fix.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
-  c->mt.lc = c->mlc;
-  c->mt.r = c->dr;
-  c->mt.s = c->ds;
+  c->mt.rec = c->mrec;
+  c->mt.dpitch = dpitch;
   c->mt.org = c->morg;
   c->mt.tile_ok = c->mok;
   c->mt.bw = bw;

@@ -68,9 +68,10 @@ struct UniformTables {
 constexpr int kMappedTileX = 32, kMappedTileY = 8;
 struct MappedTables {
   bool valid;
-  const int* lc;              // [25][nv]: (ly << 16) | lx, stencil origin inside the window
-  const float* r;             // [25][nv]: local departure coordinates in the cell
-  const float* s;
+  // departure records, [3][25][rows][dpitch] 32-bit words (rows = ny rounded up to the tile):
+  // (ly << 16) | lx, the stencil origin inside the window; r and s, the local coordinates
+  const uint32_t* rec;
+  int dpitch;
   const int2* org;            // [ntiles][25]: window origin (node column, node row)
   const unsigned char* tile_ok;
   int bw, bh;                 // window: bw vertices x bh rows

@@ -9,9 +9,10 @@
 // -xi dt.  The host computes, per tile and plane, the window's origin and the stencil origin of
 // every vertex inside it (two 16-bit offsets).  The kernel copies each plane's window of (f, g)
 // pairs into shared memory with one TMA tensor copy (the state layout carries ghost cells with
-// the periodic images, so a window never wraps), five planes per stage, three stages ahead in
-// four buffers, and every thread interpolates its vertex from shared memory: (p+1)^2 pair loads
-// per plane, weights from the local coordinates by the tail-weight polynomials, packed FP32x2
+// the periodic images, so a window never wraps), five planes per stage, plus one copy of the
+// stage's departure records (stencil origin, r, s) of the tile, two stages ahead in three
+// buffers.  Every thread then interpolates its vertex from shared memory: (p+1)^2 pair loads per
+// plane, weights from the local coordinates by the tail-weight polynomials, packed FP32x2
 // arithmetic in the difference form of the uniform kernel (constants reproduced exactly).
 // Tiles whose windows do not fit the common window size are left to the gather kernel.
 #include "kernels.h"
@@ -22,14 +23,13 @@ namespace sllbm {
 namespace {
 
 constexpr int kMNT = kMappedTileX * kMappedTileY;   // threads per CTA, one vertex each
-constexpr int kMStages = 4;                         // staging buffers (prefetch distance 3)
+constexpr int kMStages = 3;                         // staging buffers (prefetch distance 2)
+constexpr int kMDesc = 3 * kQ1 * kMNT;              // 32-bit words of one stage's records
 
 struct MappedArgs {
   CUtensorMap tmap;          // 3D map of the source state: (pair element, row, plane)
+  CUtensorMap dmap;          // 4D map of the records: (column, row, plane, field)
   StepArgs a;
-  const int* lc;             // [25][nv]: (ly << 16) | lx, stencil origin in the plane's window
-  const float* r;            // [25][nv]: local x coordinate in the departure cell
-  const float* s;            // [25][nv]: local y coordinate
   const int2* org;           // [ntiles][25]: window origin (node column, node row)
   const unsigned char* tile_ok;
   int gx, gy;                // ghost columns / rows before the interior origin
@@ -60,7 +60,8 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
   const StepArgs& a = ma.a;
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem_raw = smem_dyn + ((128 - (smem_u32(smem_dyn) & 127)) & 127);
-  Store* S = reinterpret_cast<Store*>(smem_raw);                          // [NSB][5][box]
+  uint32_t* D = reinterpret_cast<uint32_t*>(smem_raw);                    // [NSB][3][5][8][32]
+  Store* S = reinterpret_cast<Store*>(D + (size_t)NSB * kMDesc);          // [NSB][5][box]
   uint64_t* BAR = reinterpret_cast<uint64_t*>(S + (size_t)NSB * 5 * ma.box_stride);
 
   const int tid = threadIdx.x;
@@ -89,6 +90,8 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
       const int buf = (int)(s % NSB);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       mbar_expect_tx(&BAR[buf], ma.stage_bytes);
+      tma_load_4d(D + (size_t)buf * kMDesc, &ma.dmap, (tile % tiles_x) * kMappedTileX,
+                  (tile / tiles_x) * kMappedTileY, 5 * st, 0, &BAR[buf]);
       for (int b = 0; b < kQ1; ++b) {
         const int i = 5 * st + b;
         const int2 o = ma.org[(size_t)tile * kQ + i];
@@ -104,22 +107,11 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
 #pragma unroll 1
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s0 += kQ1) {
     const int x = (tile % tiles_x) * kMappedTileX + lane, y = (tile / tiles_x) * kMappedTileY + row;
-    const bool valid = x < a.nx && y < a.ny;
-    const long long v = valid ? (long long)y * a.nx + x : 0;
+    const bool store = x < a.nx && y < a.ny && __ldg(ma.tile_ok + tile);
     float2 fg[kQ];
 #pragma unroll
     for (int ph = 0; ph < kQ1; ++ph) {
       const long s = s0 + ph;
-      // this stage's descriptors (coalesced; issued before the wait so that they overlap it)
-      int lcv[kQ1];
-      float rv[kQ1], sv[kQ1];
-#pragma unroll
-      for (int b = 0; b < kQ1; ++b) {
-        const size_t d = (size_t)(5 * ph + b) * a.nv + v;
-        lcv[b] = __ldg(ma.lc + d);
-        rv[b] = __ldg(ma.r + d);
-        sv[b] = __ldg(ma.s + d);
-      }
       mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);   // stage landed
       __syncthreads();   // every thread is done with stage s - 1: its buffer can be refilled
       if (ph + PD < kQ1)
@@ -127,13 +119,14 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
       else
         issue(tile + gridDim.x, ph + PD - kQ1, s + PD);
       const Store* stage = S + (size_t)(s % NSB) * 5 * ma.box_stride;
+      const uint32_t* rec = D + (size_t)(s % NSB) * kMDesc + tid;   // [field][b][row][lane]
 #pragma unroll
       for (int b = 0; b < kQ1; ++b) {
+        const int lcv = (int)rec[b * kMNT];
         float Wx[P + 1], Wy[P + 1];
-        tail_weights<P>(wc, rv[b], Wx);
-        tail_weights<P>(wc, sv[b], Wy);
-        const Store* base = stage + (size_t)b * ma.box_stride +
-                            (size_t)(lcv[b] >> 16) * bw2 + 2 * (lcv[b] & 0xffff);
+        tail_weights<P>(wc, __uint_as_float(rec[(kQ1 + b) * kMNT]), Wx);
+        tail_weights<P>(wc, __uint_as_float(rec[(2 * kQ1 + b) * kMNT]), Wy);
+        const Store* base = stage + (size_t)b * ma.box_stride + (size_t)(lcv >> 16) * bw2 + 2 * (lcv & 0xffff);
         float2 rows[P + 1];
 #pragma unroll
         for (int kb = 0; kb <= P; ++kb) {
@@ -154,7 +147,7 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
       }
     }
     const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
-    if (valid && ma.tile_ok[tile]) {
+    if (store) {
       if (!ok) atomicOr(a.flag, 1);
       Store* dst = static_cast<Store*>(a.dst);
       store_images(a.ghost, x, y, [&](int xx, int yy) {
@@ -179,7 +172,7 @@ static int box_stride_elems(int bw, int bh) {
 size_t mapped_smem_bytes(int bw, int bh, int store) {
   const int st = store == kStoreBF16 ? box_stride_elems<__nv_bfloat16>(bw, bh) * 2
                                      : box_stride_elems<float>(bw, bh) * 4;
-  return 128 + (size_t)kMStages * 5 * st + sizeof(uint64_t) * kMStages;
+  return 128 + (size_t)kMStages * (5 * st + 4 * kMDesc) + sizeof(uint64_t) * kMStages;
 }
 
 template <int P, typename Store>
@@ -188,9 +181,6 @@ static cudaError_t launch_p(const StepArgs& a, const MappedTables& t, cudaStream
   MappedArgs ma;
   memset(&ma, 0, sizeof(ma));
   ma.a = a;
-  ma.lc = t.lc;
-  ma.r = t.r;
-  ma.s = t.s;
   ma.org = t.org;
   ma.tile_ok = t.tile_ok;
   ma.gx = t.gx;
@@ -198,7 +188,7 @@ static cudaError_t launch_p(const StepArgs& a, const MappedTables& t, cudaStream
   ma.bw = t.bw;
   ma.bh = t.bh;
   ma.box_stride = box_stride_elems<Store>(t.bw, t.bh);
-  ma.stage_bytes = (unsigned)(5 * 2 * t.bw * t.bh * sizeof(Store));
+  ma.stage_bytes = (unsigned)(5 * 2 * t.bw * t.bh * sizeof(Store) + 4 * kMDesc);
   for (int al = 0; al < 4; ++al)
     for (int j = 0; j < 5; ++j) ma.wc[al][j] = t.wc[al][j];
   EncodeTiledFn enc = encode_fn();
@@ -214,6 +204,17 @@ static cudaError_t launch_p(const StepArgs& a, const MappedTables& t, cudaStream
                    3, const_cast<char*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  // records: [field][plane][row][column] 32-bit words, rows of dpitch columns
+  const int rows = (a.ny + kMappedTileY - 1) / kMappedTileY * kMappedTileY;
+  const cuuint64_t ddims[4] = {(cuuint64_t)t.dpitch, (cuuint64_t)rows, (cuuint64_t)kQ, 3u};
+  const cuuint64_t dstrides[3] = {(cuuint64_t)t.dpitch * 4, (cuuint64_t)t.dpitch * rows * 4,
+                                  (cuuint64_t)t.dpitch * rows * kQ * 4};
+  const cuuint32_t dbox[4] = {(cuuint32_t)kMappedTileX, (cuuint32_t)kMappedTileY, 5u, 3u};
+  const cuuint32_t destr[4] = {1u, 1u, 1u, 1u};
+  r = enc(&ma.dmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<uint32_t*>(t.rec), ddims, dstrides,
+          dbox, destr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const size_t smem = mapped_smem_bytes(t.bw, t.bh, sizeof(Store) == 2 ? kStoreBF16 : kStoreF32);
   cudaError_t e = cudaFuncSetAttribute(step_mapped_kernel<P, Store>,
