@@ -230,31 +230,33 @@ __device__ __forceinline__ T eq_em1(const EqFactors<T>& e, int a, int b) {
 // S_{4-k}(b))): after a per-vertex set-up of 45 factors, five FMAs per velocity.
 __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Consts& cs,
                                                       const CollideK& cp) {
-  // moments (Sec. II): rho = 1 + sum fbar, j = sum fbar xi, A2 = sum fbar |xi|^2, G = sum gbar
-  float rowsum[kQ1], colsum[kQ1];
+  // moments (Sec. II): rho = 1 + sum fbar, j = sum fbar xi, A2 = sum fbar |xi|^2, G = sum gbar.
+  // Row and column sums of the (f, g) pairs in packed FP32x2: rs[a] = (sum_b f_ab, sum_b g_ab).
+  float2 rs[kQ1], cl[kQ1];
 #pragma unroll
-  for (int a = 0; a < kQ1; ++a) rowsum[a] = 0.f;
+  for (int a = 0; a < kQ1; ++a) {
+    rs[a] = fg[5 * a];
 #pragma unroll
-  for (int b = 0; b < kQ1; ++b) colsum[b] = 0.f;
+    for (int b = 1; b < kQ1; ++b) rs[a] = __fadd2_rn(rs[a], fg[5 * a + b]);
+  }
 #pragma unroll
-  for (int a = 0; a < kQ1; ++a)
+  for (int b = 0; b < kQ1; ++b) {
+    cl[b] = fg[b];
 #pragma unroll
-    for (int b = 0; b < kQ1; ++b) {
-      rowsum[a] += fg[5 * a + b].x;
-      colsum[b] += fg[5 * a + b].x;
-    }
+    for (int a = 1; a < kQ1; ++a) cl[b] = __fadd2_rn(cl[b], fg[5 * a + b]);
+  }
   float drho = 0.f, jx = 0.f, jy = 0.f, a2 = 0.f;
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
-    drho += rowsum[a];
-    jx += cs.xif[a] * rowsum[a];
-    jy += cs.xif[a] * colsum[a];
-    a2 += cs.xif[a] * cs.xif[a] * (rowsum[a] + colsum[a]);
+    drho += rs[a].x;
+    jx += cs.xif[a] * rs[a].x;
+    jy += cs.xif[a] * cl[a].x;
+    a2 += cs.xif[a] * cs.xif[a] * (rs[a].x + cl[a].x);
   }
   float G = 0.f;
   if (cp.npop == 2) {
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) G += fg[i].y;
+    for (int a = 0; a < kQ1; ++a) G += rs[a].y;
   }
   const float rho = 1.f + drho;
   const float inv_rho = 1.f / rho;
@@ -270,9 +272,12 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
   ay[2] = uy * uy + q;
   ay[3] = uy * (uy * uy + 3.f * q);
   ay[4] = uy * uy * (uy * uy + 6.f * q) + 3.f * q * q;
-  float Xw[4][kQ1], Sw[4][kQ1], Bb[kQ1];
+  // The 1D nodes are 0, +s, +l, -s, -l: component a + 2 (a = 1, 2) mirrors a, so with
+  // He_k(-xi) = (-1)^k He_k(xi) its X_k(a + 2) is (-1)^k X_k(a), and X_k(0) = 0 for odd k.  Only
+  // a = 0, 1, 2 are formed; each mirrored pair takes even part +- odd part.
+  float Xw[4][3], Sw[4][kQ1], Bb[kQ1];
 #pragma unroll
-  for (int a = 0; a < kQ1; ++a) {
+  for (int a = 0; a < 3; ++a) {
     const float rw = rho * cs.wf[a];
 #pragma unroll
     for (int k = 1; k <= 4; ++k) Xw[k - 1][a] = rw * (ax[k] * cs.hef[k][a]);
@@ -293,34 +298,49 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
   // the equilibrium has the moments of the pre-collision state; in FP32 its fourth-order
   // polynomial carries rounding of the size of its largest terms, which would leak into the
   // conserved moments every step.
-  float erow[kQ1], ecol[kQ1], eg = 0.f, KqW[kQ1];
+  // The sums of the equilibrium follow the grouping and order of the pre-collision sums (rows,
+  // columns, g by rows), so that their FP32 rounding errors largely cancel in the residuals.
+  float erow[kQ1], ecol[kQ1], egrow[kQ1], KqW[kQ1];
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
     erow[a] = 0.f;
     ecol[a] = 0.f;
+    egrow[a] = 0.f;
     KqW[a] = Kq * cs.wf[a];
   }
   // The g lanes are computed whatever the population count (with one population they hold
   // zeros and are never stored); f and g relax together in packed FP32x2 arithmetic.
   const float2 keep2 = bcast2(keep), om2 = bcast2(om);
+  // g^eq - K w = K ((1 + q)(f^eq - w) + q w)   (g^eq = K theta f^eq, Sec. II.D); t = K q w_a w_b
+  auto relax = [&](int a, int b, float ef, float t) {
+    erow[a] += ef;
+    ecol[b] += ef;
+    const float egi = Kq1 * ef + t;
+    egrow[a] += egi;
+    fg[5 * a + b] = fma2(keep2, fg[5 * a + b], __fmul2_rn(om2, make_float2(ef, egi)));
+  };
 #pragma unroll
-  for (int a = 0; a < kQ1; ++a)
+  for (int b = 0; b < kQ1; ++b) {
+    // f^eq - w for (a, b): w_a B(b) + sum_k X_k(a) S_{4-k}(b), even k and odd k apart
+    float ev[3], od[3], t[3];
 #pragma unroll
-    for (int b = 0; b < kQ1; ++b) {
-      const int i = 5 * a + b;
-      float ef = cs.wf[a] * Bb[b];                        // f^eq - w
-#pragma unroll
-      for (int k = 1; k <= 4; ++k) ef += Xw[k - 1][a] * Sw[4 - k][b];
-      erow[a] += ef;
-      ecol[b] += ef;
-      // g^eq - K w = K ((1 + q)(f^eq - w) + q w)   (g^eq = K theta f^eq, Sec. II.D)
-      const float egi = Kq1 * ef + cs.wf[a] * KqW[b];
-      eg += egi;
-      fg[i] = fma2(keep2, fg[i], __fmul2_rn(om2, make_float2(ef, egi)));
+    for (int a = 1; a <= 2; ++a) {
+      ev[a] = cs.wf[a] * Bb[b] + Xw[1][a] * Sw[2][b] + Xw[3][a] * Sw[0][b];
+      od[a] = Xw[0][a] * Sw[3][b] + Xw[2][a] * Sw[1][b];
+      t[a] = cs.wf[a] * KqW[b];
     }
+    relax(0, b, cs.wf[0] * Bb[b] + Xw[1][0] * Sw[2][b] + Xw[3][0] * Sw[0][b], cs.wf[0] * KqW[b]);
+    relax(1, b, ev[1] + od[1], t[1]);
+    relax(2, b, ev[2] + od[2], t[2]);
+    relax(3, b, ev[1] - od[1], t[1]);
+    relax(4, b, ev[2] - od[2], t[2]);
+  }
   // Residual moments of (equilibrium - pre-collision state); remove them with the smallest
   // correction in the span of w {1, xi_x, xi_y} (mass, momentum) and w on g (energy).  This
   // changes nothing in exact arithmetic and restores conservation to the rounding of the sums.
+  float eg = 0.f;
+#pragma unroll
+  for (int a = 0; a < kQ1; ++a) eg += egrow[a];
   float r0 = -drho, r1 = -jx, r2 = -jy, r3 = -(a2 + G) + (cp.npop == 2 ? eg : 0.f);
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
@@ -330,7 +350,8 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
     r3 += cs.xif[a] * cs.xif[a] * (erow[a] + ecol[a]);
   }
   const float c3 = r3 - 2.f * r0;   // energy residual left after the mass correction
-  // per b: w_b r2 xi_b and w_b c3, so that each velocity takes three FMAs
+  // per b: w_b r2 xi_b and w_b c3, so that each velocity takes three FMAs (the g term is shared
+  // by a component and its mirror)
   float r2w[kQ1], c3w[kQ1];
 #pragma unroll
   for (int b = 0; b < kQ1; ++b) {
@@ -338,15 +359,19 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
     c3w[b] = c3 * cs.wf[b];
   }
 #pragma unroll
-  for (int a = 0; a < kQ1; ++a) {
+  for (int a = 0; a <= 2; ++a) {
     const float ta = om * cs.wf[a];
-    const float ca = r0 + r1 * cs.xif[a];
+    const float ca = r0 + r1 * cs.xif[a], cm = r0 - r1 * cs.xif[a];
 #pragma unroll
     for (int b = 0; b < kQ1; ++b) {
-      const int i = 5 * a + b;
       // om w_a w_b (r0 + r1 xi_a + r2 xi_b) on f, om w_a w_b c3 on g
-      fg[i].x -= ta * (ca * cs.wf[b] + r2w[b]);
-      fg[i].y -= ta * c3w[b];
+      const float tg = ta * c3w[b];
+      fg[5 * a + b].x -= ta * (ca * cs.wf[b] + r2w[b]);
+      fg[5 * a + b].y -= tg;
+      if (a > 0) {
+        fg[5 * (a + 2) + b].x -= ta * (cm * cs.wf[b] + r2w[b]);
+        fg[5 * (a + 2) + b].y -= tg;
+      }
     }
   }
   if (cp.npop != 2) {

@@ -70,11 +70,14 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
   const bool two = a.cp.npop == 2;
   const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
   if (!ok) atomicOr(a.flag, 1);
+  if (!two) {   // one population: the g slots stay zero
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) fg[i].y = 0.f;
+  }
   store_images(a.ghost, ix, iy, [&](int xx, int yy) {
     Store* o = dst + (ptrdiff_t)yy * a.pitch + 2 * (ptrdiff_t)xx;
 #pragma unroll
-    for (int i = 0; i < kQ; ++i)
-      st_pair(o + (ptrdiff_t)i * a.plane_stride, two ? fg[i] : make_float2(fg[i].x, 0.f));
+    for (int i = 0; i < kQ; ++i, o += a.plane_stride) st_pair(o, fg[i]);
   });
 }
 

@@ -280,11 +280,14 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
     if (x < a.nx && y < a.ny && ua.std_x[x] && ua.std_y[y]) {
       if (!ok) atomicOr(a.flag, 1);
       Store* dst = static_cast<Store*>(a.dst);
+      if (!two) {   // one population: the g slots stay zero
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) fg[i].y = 0.f;
+      }
       store_images(a.ghost, x, y, [&](int xx, int yy) {
         Store* o = dst + (ptrdiff_t)yy * a.pitch + 2 * (ptrdiff_t)xx;
 #pragma unroll
-        for (int i = 0; i < kQ; ++i)
-          st_pair(o + (ptrdiff_t)i * a.plane_stride, two ? fg[i] : make_float2(fg[i].x, 0.f));
+        for (int i = 0; i < kQ; ++i, o += a.plane_stride) st_pair(o, fg[i]);
       });
     }
   }
