@@ -15,15 +15,15 @@
 // 64-bit shared-memory and global accesses, packed FP32x2 FMAs.
 //
 // Persistent CTAs (two per SM by default, or one with the tall tile) walk over tiles of 32 x TY
-// vertices (TY a multiple of p), one vertex per thread.  The 25 pair planes of a tile are done in 5 stages, one per x component
-// a.  A stage (the 5 planes b = 0..4) is copied into shared memory by one TMA tensor copy (tile +
+// vertices (TY a multiple of p), one vertex per thread.  The 25 pair planes of a tile are done in
+// 5 stages, one per x component a.  A stage (the 5 planes b = 0..4) is copied into shared memory by one TMA tensor copy (tile +
 // stencil halo; the state layout carries ghost cells with the periodic images, so a tile never
 // wraps), completing on an mbarrier, three stages ahead in four buffers.  Phase k runs the y pass
 // of stage k (task = plane b, staged column, chunk of rows: register window of the column) and
-// the x pass of stage k-1 (thread = vertex): six barriers per tile.  After stage 4 every thread
+// the x pass of stage k-1 (thread = vertex): five barriers per tile.  After stage 4 every thread
 // holds the 50 pre-collision deviations of its vertex, collides in registers and writes 25
-// coalesced rows of pairs (plus periodic images in the ghost cells), while the first stages
-// of its next tile are already in flight.
+// coalesced rows of pairs (plus periodic images in the ghost cells), in the phase that runs the
+// y pass of the next tile's first stage.
 //
 // Interpolation form: sum_alpha w_alpha v_{s+alpha} is evaluated as
 //   v_s + sum_{alpha >= 1} W_alpha (v_{s+alpha} - v_{s+alpha-1}),  W_alpha = sum_{beta >= alpha} w_beta,
@@ -228,31 +228,43 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
 
 #pragma unroll
   for (int k = 0; k < PD; ++k) issue(blockIdx.x, k, k);
-  long s0 = 0;   // global index of stage 0 of the current tile
+  // Phase s (global stage counter) runs the y pass of stage s and the x pass of stage s - 1; when
+  // that was the last stage of a tile, the tile collides and stores in the same phase, next to
+  // the y pass of the following tile's first stage: five barriers per tile, and the FMA-heavy
+  // collision of some warps overlaps the shared-memory-heavy y pass of others.
+  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  int x = 0, y = 0;   // vertex of the tile in the x pass
+  float2 fg[kQ];      // (f, g) after streaming, velocity i = 5a + b
 #pragma unroll 1
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, s0 += kQ1) {
-    const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * TY;
-    const int x = x0 + lane, y = y0 + row;
-    float2 fg[kQ];   // (f, g) after streaming, velocity i = 5a + b
+  for (int k = 0; k <= my_tiles; ++k) {
+    const int tile = blockIdx.x + k * gridDim.x;   // tile of the y pass
+    const bool ycur = k < my_tiles;
 #pragma unroll
-    for (int ph = 0; ph <= kQ1; ++ph) {
-      const long s = s0 + ph;
-      if (ph < kQ1) mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);  // stage landed
+    for (int j = 0; j < kQ1; ++j) {
+      if (!ycur && j > 0) break;   // after the last tile: its x pass of stage 4 and collision
+      const long s = (long)kQ1 * k + j;
+      if (ycur) mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);  // stage landed
       __syncthreads();  // T[(s-1)&1] written; T[s&1] and S[(s+PD)%NSB] no longer read
-      if (ph + PD < kQ1)
-        issue(tile, ph + PD, s + PD);
-      else if (ph < kQ1)
-        issue(tile + gridDim.x, ph + PD - kQ1, s + PD);   // the next tile's first stages
-      if (ph < kQ1)
+      if (ycur) {
+        if (j + PD < kQ1)
+          issue(tile, j + PD, s + PD);
+        else
+          issue(tile + gridDim.x, j + PD - kQ1, s + PD);   // the next tile's first stages
         y_pass<P, Tall, Store>(S + (size_t)(s % NSB) * BS::STRIDE, T + (size_t)(s & 1) * kQ1 * TY * kTC,
                                WY, EY);
+      }
+      if (k == 0 && j == 0) continue;   // no stage before the first
 
-      // ---- x pass of stage ph-1: thread = vertex; exact taps of (a, k = x mod p) ----
-      if (ph >= 1) {
-        const int st = ph - 1;
-        const int k = x % P;
-        const float2* w = WX + (st * P + k) * 4;
-        const int cbase = lane + kCO + DX[st * P + k];
+      // ---- x pass of stage s-1 (component st): thread = vertex; taps of (a, x mod p) ----
+      const int st = (j + kQ1 - 1) % kQ1;
+      if (j == 1) {   // stage 0 of tile k: this thread's vertex
+        x = (tile % tiles_x) * 32 + lane;
+        y = (tile / tiles_x) * TY + row;
+      }
+      {
+        const int kx = x % P;
+        const float2* w = WX + (st * P + kx) * 4;
+        const int cbase = lane + kCO + DX[st * P + kx];
         float2 W[P + 1];
         int tp[P + 1];   // T positions of the stencil columns
 #pragma unroll
@@ -274,21 +286,23 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
           fg[5 * st + b] = acc;
         }
       }
-    }
+      if (j != 0) continue;
 
-    const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
-    if (x < a.nx && y < a.ny && ua.std_x[x] && ua.std_y[y]) {
-      if (!ok) atomicOr(a.flag, 1);
-      Store* dst = static_cast<Store*>(a.dst);
-      if (!two) {   // one population: the g slots stay zero
+      // ---- the tile of the x pass is complete: collide and store ----
+      const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
+      if (x < a.nx && y < a.ny && ua.std_x[x] && ua.std_y[y]) {
+        if (!ok) atomicOr(a.flag, 1);
+        Store* dst = static_cast<Store*>(a.dst);
+        if (!two) {   // one population: the g slots stay zero
 #pragma unroll
-        for (int i = 0; i < kQ; ++i) fg[i].y = 0.f;
+          for (int i = 0; i < kQ; ++i) fg[i].y = 0.f;
+        }
+        store_images(a.ghost, x, y, [&](int xx, int yy) {
+          Store* o = dst + (ptrdiff_t)yy * a.pitch + 2 * (ptrdiff_t)xx;
+#pragma unroll
+          for (int i = 0; i < kQ; ++i, o += a.plane_stride) st_pair(o, fg[i]);
+        });
       }
-      store_images(a.ghost, x, y, [&](int xx, int yy) {
-        Store* o = dst + (ptrdiff_t)yy * a.pitch + 2 * (ptrdiff_t)xx;
-#pragma unroll
-        for (int i = 0; i < kQ; ++i, o += a.plane_stride) st_pair(o, fg[i]);
-      });
     }
   }
 }
