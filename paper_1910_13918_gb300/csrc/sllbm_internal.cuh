@@ -292,32 +292,33 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
     }
     Bb[b] = cs.wf[b] * (drho + rho * acc);
   }
-  const float om = cp.omegaf, keep = 1.f - cp.omegaf;
+  const float om = cp.omegaf;
   const float Kq1 = cp.Kf * (1.f + q), Kq = cp.Kf * q;
-  // Post-collision values, and the moments of the FP32 equilibrium itself.  In exact arithmetic
-  // the equilibrium has the moments of the pre-collision state; in FP32 its fourth-order
-  // polynomial carries rounding of the size of its largest terms, which would leak into the
-  // conserved moments every step.
-  // The sums of the equilibrium follow the grouping and order of the pre-collision sums (rows,
-  // columns, g by rows), so that their FP32 rounding errors largely cancel in the residuals.
-  float erow[kQ1], ecol[kQ1], egrow[kQ1], KqW[kQ1];
+  // Post-collision values f + omega (f^eq - f), and the moments of (f^eq - f) itself.  In exact
+  // arithmetic the equilibrium has the moments of the pre-collision state; in FP32 its
+  // fourth-order polynomial carries rounding of the size of its largest terms, which would leak
+  // into the conserved moments every step.  The residuals are summed from the differences
+  // f^eq - f (small, and mostly exact in FP32), not as differences of two sums of full-size
+  // values: at omega near 2 the state is almost 2-periodic in time, the roundings of such sums
+  // repeat every other step, and their mismatch would add up to a steady drift of the moments.
+  float2 drow[kQ1];   // sum_b (f^eq - f, g^eq - g) of row a
+  float dcol[kQ1], KqW[kQ1];
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
-    erow[a] = 0.f;
-    ecol[a] = 0.f;
-    egrow[a] = 0.f;
+    drow[a] = make_float2(0.f, 0.f);
+    dcol[a] = 0.f;
     KqW[a] = Kq * cs.wf[a];
   }
   // The g lanes are computed whatever the population count (with one population they hold
   // zeros and are never stored); f and g relax together in packed FP32x2 arithmetic.
-  const float2 keep2 = bcast2(keep), om2 = bcast2(om);
+  const float2 om2 = bcast2(om);
   // g^eq - K w = K ((1 + q)(f^eq - w) + q w)   (g^eq = K theta f^eq, Sec. II.D); t = K q w_a w_b
   auto relax = [&](int a, int b, float ef, float t) {
-    erow[a] += ef;
-    ecol[b] += ef;
     const float egi = Kq1 * ef + t;
-    egrow[a] += egi;
-    fg[5 * a + b] = fma2(keep2, fg[5 * a + b], __fmul2_rn(om2, make_float2(ef, egi)));
+    const float2 d = sub2(make_float2(ef, egi), fg[5 * a + b]);
+    drow[a] = __fadd2_rn(drow[a], d);
+    dcol[b] += d.x;
+    fg[5 * a + b] = fma2(om2, d, fg[5 * a + b]);
   };
 #pragma unroll
   for (int b = 0; b < kQ1; ++b) {
@@ -338,17 +339,16 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
   // Residual moments of (equilibrium - pre-collision state); remove them with the smallest
   // correction in the span of w {1, xi_x, xi_y} (mass, momentum) and w on g (energy).  This
   // changes nothing in exact arithmetic and restores conservation to the rounding of the sums.
-  float eg = 0.f;
-#pragma unroll
-  for (int a = 0; a < kQ1; ++a) eg += egrow[a];
-  float r0 = -drho, r1 = -jx, r2 = -jy, r3 = -(a2 + G) + (cp.npop == 2 ? eg : 0.f);
+  float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, rg = 0.f;
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
-    r0 += erow[a];
-    r1 += cs.xif[a] * erow[a];
-    r2 += cs.xif[a] * ecol[a];
-    r3 += cs.xif[a] * cs.xif[a] * (erow[a] + ecol[a]);
+    r0 += drow[a].x;
+    r1 += cs.xif[a] * drow[a].x;
+    r2 += cs.xif[a] * dcol[a];
+    r3 += cs.xif[a] * cs.xif[a] * (drow[a].x + dcol[a]);
+    rg += drow[a].y;
   }
+  if (cp.npop == 2) r3 += rg;
   const float c3 = r3 - 2.f * r0;   // energy residual left after the mass correction
   // per b: w_b r2 xi_b and w_b c3, so that each velocity takes three FMAs (the g term is shared
   // by a component and its mirror)

@@ -89,6 +89,8 @@ class Workload:
             return max(math.hypot(st[1], st[2]) for st in states.values())
         if self.kind == "svi":
             return self.extra["Ma_A"]
+        if self.kind == "sdp":
+            return self.extra["U"]
         return 1.0
 
     def fields(self, x, y, perturb=False):
@@ -214,7 +216,18 @@ def _svi(w, x, y):
     return rho, u, v, p / rho
 
 
-_GENERATORS = {"tgv": _tgv, "sod": _sod, "riemann": _riemann, "svi": _svi}
+def _sdp(w, x, y):
+    rho = sdp_density(w, x, y, 0.0)
+    return rho, np.full_like(x, w.extra["U"]), np.zeros_like(x), 1.0 / rho   # P = 1
+
+
+def sdp_density(w: Workload, x, y, t):
+    """Exact density of the smooth density propagation at lattice time t: the initial wave
+    1 + 0.2 sin(pi x) sin(pi y) carried along x with the uniform speed U."""
+    return 1.0 + 0.2 * np.sin(np.pi * (x - w.extra["U"] * t)) * np.sin(np.pi * y)
+
+
+_GENERATORS = {"tgv": _tgv, "sod": _sod, "riemann": _riemann, "svi": _svi, "sdp": _sdp}
 
 
 def svi_envelope(w: Workload, x, y):
@@ -303,5 +316,28 @@ def svi():
                            "x_shock": 0.5, "x_objective": 1.5, "checkpoint_every": 20})
 
 
+def sdp(points=16, step_factor=1):
+    """Smooth density propagation (Sec. III.B, Table II) on [-1,1]^2, periodic, p = 4, with
+    points x points vertices (points / 4 cells per axis).
+
+    Reading of the paper's units: the speed is U = Ma c_s = 0.2 (c_s = 1), so the wave crosses
+    the domain once (the paper's t = 2 at unit speed) in lattice time 2 / U = 10.  The paper's
+    1105 steps at 16 x 16 points match dt = 0.5 h_min / |c|max with the smallest GLC spacing
+    h_min = 0.5 (1 - cos(pi / 4)) / 2 = 0.0732 (10 / 0.00906 = 1104); the step count doubles
+    with each doubling of the resolution.  nu = 1e-10, so tau = nu / dt + 1/2 is 1/2 to 1e-8.
+    P = 1, so T = 1 / rho."""
+    cells = points // 4
+    steps = 1105 * (points // 16) * step_factor
+    U, t_end, nu = 0.2, 10.0, 1e-10
+    dt = t_end / steps
+    return Workload(f"sdp{points}_p4", cells, cells, 4, -1.0, 1.0, -1.0, 1.0, PERIODIC, PERIODIC,
+                    dt, nu / dt + 0.5, steps, "sdp", seed=7, extra={"U": U, "t_end": t_end})
+
+
+# The smooth-density-propagation errors of the paper's Table II: max |rho - rho_ref| at t_end.
+SDP_TABLE_II = {16: 2.10599e-2, 32: 1.32533e-3, 64: 5.36948e-5, 128: 4.68312e-6, 256: 7.90318e-7,
+                512: 2.14017e-7}
+
+
 ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
-       "riemann_paper": riemann_paper, "svi": svi}
+       "riemann_paper": riemann_paper, "svi": svi, "sdp": sdp}
