@@ -334,10 +334,5 @@ def sdp(points=16, step_factor=1):
                     dt, nu / dt + 0.5, steps, "sdp", seed=7, extra={"U": U, "t_end": t_end})
 
 
-# The smooth-density-propagation errors of the paper's Table II: max |rho - rho_ref| at t_end.
-SDP_TABLE_II = {16: 2.10599e-2, 32: 1.32533e-3, 64: 5.36948e-5, 128: 4.68312e-6, 256: 7.90318e-7,
-                512: 2.14017e-7}
-
-
 ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
        "riemann_paper": riemann_paper, "svi": svi, "sdp": sdp}

@@ -5,6 +5,8 @@ the initial fields on its own vertex coordinates.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from oracle import sllbm as o
@@ -115,3 +117,19 @@ def _sod_small():
 def _svi_small():
     w = W.svi().resized(24, 12, steps=100, dt=0.01)
     return w
+
+
+def table2():
+    """The paper's smooth-density-propagation errors (Sec. III.B, Table II), tests/golden."""
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "sdp_table2.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                n, err, _ = line.split()
+                out[int(n)] = float(err)
+    return out
+
+
+def sdp_error(w: W.Workload, rho, x, y):
+    """max |rho - rho_exact| at the end of a smooth-density-propagation run."""
+    return float(np.max(np.abs(rho - W.sdp_density(w, x, y, w.extra["t_end"]))))
