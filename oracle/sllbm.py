@@ -16,7 +16,10 @@ populations, not deviations).
 Readings of points the paper leaves open (each is also listed in the design notes):
 * collide at vertices, store post-collision values, interpolate that field at departure points
   (pull streaming of post-collision populations, Eq. 12 with Eq. 13);
-* Prandtl number 1, so the quasi-equilibrium term of Eq. 12 vanishes (tau_Pr = tau);
+* Prandtl number 1 unless asked otherwise, so the quasi-equilibrium term of Eq. 12 vanishes
+  (tau_Pr = tau); for Pr != 1 the quasi-equilibrium f* of Sec. II.C is read with the 1/3! of the
+  Hermite normalisation (w_i Q^neq : H^(3)(xi_i) / 3!, whose third moment is Q^neq), and g* as
+  the same third-order projection of g's own centred third moment;
 * temperature from the moments: T = (sum f|xi|^2 + sum g - rho |u|^2) / (2 C_v rho), T0 = 1;
 * zero-gradient boundaries clamp the departure point into the domain; periodic ones wrap it;
 * departure points exactly on a cell face belong to the cell on their right, and the upper end of
@@ -187,15 +190,54 @@ def total_energy_density(f, g):
 # ---------------------------------------------------------------------------------------------
 # Collision (Eq. streaming_fg with Pr = 1)
 # ---------------------------------------------------------------------------------------------
-def collide(f, g, tau, cv):
-    """BGK relaxation at the vertices: f* = f - (f - f^eq)/tau, the same for g.
+def centered_third_moment(F, u):
+    """Centred third moment Q[a, b, c] = sum_i F_i (xi_i - u)_a (xi_i - u)_b (xi_i - u)_c of a
+    population field (the centred heat-flux tensor of Sec. II.C), shape (D, D, D) + vertex shape.
+    ``u`` has the vertex shape plus a trailing D axis."""
+    xi, _ = d2q25()
+    out = np.zeros((D, D, D) + F.shape[1:], dtype=F.dtype)
+    for i in range(Q):
+        c = [xi[i, k] - u[..., k] for k in range(D)]
+        for a, b, cc in itertools.product(range(D), repeat=3):
+            out[a, b, cc] = out[a, b, cc] + F[i] * c[a] * c[b] * c[cc]
+    return out
 
-    With Pr = 1, tau_Pr = tau and the quasi-equilibrium term of Eq. streaming_fg is zero.
+
+def quasi_equilibrium(Qneq):
+    """f*_i = w_i Q^neq : H^(3)(xi_i) / 3! (Sec. II.C): the full contraction over the D^3 index
+    tuples of the non-equilibrium centred third moment with the third Hermite tensor, weighted by
+    the lattice weight.  The 1/3! is the Hermite normalisation of the third-order term (the
+    printed formula has no prefactor); with it the third moment of f* is Q^neq."""
+    xi, w = d2q25()
+    out = np.zeros((Q,) + Qneq.shape[3:], dtype=Qneq.dtype)
+    for i in range(Q):
+        acc = np.zeros(Qneq.shape[3:], dtype=Qneq.dtype)
+        for idx in itertools.product(range(D), repeat=3):
+            acc = acc + Qneq[idx] * hermite(3, idx, xi[i])
+        out[i] = w[i] * acc / math.factorial(3)
+    return out
+
+
+def tau_prandtl(tau, pr):
+    """tau_Pr = (tau - 1/2) / Pr + 1/2 (Sec. II.D)."""
+    return (tau - 0.5) / pr + 0.5
+
+
+def collide(f, g, tau, cv, pr=1.0):
+    """Collision at the vertices (Eq. streaming_fg):
+    f* = f - (f - f^eq)/tau + (1/tau - 1/tau_Pr) f^qe, the same for g with g^eq = (2 C_v - D) theta
+    f^eq, where f^qe (g^qe) is the quasi-equilibrium of the non-equilibrium centred third moment
+    of f (of g).  With Pr = 1, tau_Pr = tau and the quasi-equilibrium term is zero: plain BGK.
     """
     rho, u, theta = macroscopic(f, g, cv)
     feq = equilibrium_f(rho, u, theta)
     geq = (2.0 * cv - D) * theta * feq
-    return f - (f - feq) / tau, g - (g - geq) / tau
+    fn, gn = f - (f - feq) / tau, g - (g - geq) / tau
+    if pr != 1.0:
+        c = 1.0 / tau - 1.0 / tau_prandtl(tau, pr)
+        fn = fn + c * quasi_equilibrium(centered_third_moment(f, u) - centered_third_moment(feq, u))
+        gn = gn + c * quasi_equilibrium(centered_third_moment(g, u) - centered_third_moment(geq, u))
+    return fn, gn
 
 
 def initial_state(rho, u, v, T, cv):
@@ -429,16 +471,16 @@ def stream(F, dep: Departures):
     return out
 
 
-def step(f, g, dep: Departures, tau, cv):
+def step(f, g, dep: Departures, tau, cv, pr=1.0):
     """One SLLBM time step: pull the post-collision populations, then collide at every vertex."""
     fpre = stream(f, dep)
     gpre = stream(g, dep)
-    return collide(fpre, gpre, tau, cv)
+    return collide(fpre, gpre, tau, cv, pr)
 
 
-def run(f, g, dep: Departures, tau, cv, nsteps):
+def run(f, g, dep: Departures, tau, cv, nsteps, pr=1.0):
     for _ in range(nsteps):
-        f, g = step(f, g, dep, tau, cv)
+        f, g = step(f, g, dep, tau, cv, pr)
     return f, g
 
 

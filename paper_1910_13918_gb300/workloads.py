@@ -52,6 +52,7 @@ class Workload:
     kind: str                      # which initial field generator
     map_a: float = 0.0             # sine-map amplitude (0: uniform grid)
     cv: float = CV
+    pr: float = 1.0                # Prandtl number (1: plain BGK, Sec. II.C)
     nodes: str = "glc"
     seed: int = 0
     extra: dict = dataclasses.field(default_factory=dict)
@@ -316,6 +317,14 @@ def svi():
                            "x_shock": 0.5, "x_objective": 1.5, "checkpoint_every": 20})
 
 
+def svi_pr():
+    """The shock-vortex workload at the paper's Prandtl number 0.75 (Sec. III.E, Sec. II.C)."""
+    w = svi()
+    w.name = "svi512x256_p2_mapped_pr075"
+    w.pr = 0.75
+    return w
+
+
 def sdp(points=16, step_factor=1):
     """Smooth density propagation (Sec. III.B, Table II) on [-1,1]^2, periodic, p = 4, with
     points x points vertices (points / 4 cells per axis).
@@ -335,4 +344,4 @@ def sdp(points=16, step_factor=1):
 
 
 ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
-       "riemann_paper": riemann_paper, "svi": svi, "sdp": sdp}
+       "riemann_paper": riemann_paper, "svi": svi, "svi_pr": svi_pr, "sdp": sdp}
