@@ -78,11 +78,16 @@ typedef struct {
 
 /* Time step, relaxation time tau = nu / (c_s^2 dt) + 1/2 (Sec. II.D), heat capacity C_v
  * (gamma = 1 + 1/C_v with R = 1; C_v = D/2 = 1 leaves g identically zero and the library then
- * carries f only), reference temperature T0 (must be 1: c_s^2 = R T0 = 1), precision. */
+ * carries f only), reference temperature T0 (must be 1: c_s^2 = R T0 = 1), precision, and the
+ * Prandtl number pr (Sec. II.C, Eq. streaming_fg): 1 (or 0, which reads as 1) is plain BGK;
+ * any other positive value adds (1/tau - 1/tau_Pr) f^qe, tau_Pr = (tau - 1/2)/Pr + 1/2, with the
+ * quasi-equilibrium f^qe_i = w_i Q^neq : H^(3)(xi_i) / 3! of the non-equilibrium centred third
+ * moment (and the same projection of g's own for g).  The adjoint covers Pr = 1 only. */
 typedef struct {
     int velset;                 /* sllbm_velset */
     double dt, tau, cv, T0;
     int prec;                   /* sllbm_prec   */
+    double pr;                  /* Prandtl number; 0 or 1: plain BGK */
 } sllbm_params;
 
 typedef struct sllbm_ctx sllbm_ctx;  /* opaque, library-owned */
@@ -154,7 +159,8 @@ sllbm_status sllbm_set_state(sllbm_ctx* ctx, const void* src_dev);
  * collision Jacobian at the pre-collision moments of that step, given as saved_moments
  * [4][ny][nx] FP32 = (rho, u, v, theta) -- exactly what sllbm_moments returns for the state the
  * step produced.  S^T is applied as a gather (pull) over precomputed transposed stencils: no
- * atomics, deterministic.  Works in every precision mode (FP32 arithmetic). */
+ * atomics, deterministic.  Works in every precision mode (FP32 arithmetic); a context with
+ * Pr != 1 gets SLLBM_ERR_UNSUPPORTED. */
 sllbm_status sllbm_adjoint_step(sllbm_ctx* ctx, const float* lambda_in_dev, float* lambda_out_dev,
                                 const float* saved_moments_dev);
 

@@ -43,6 +43,9 @@ struct CollideK {
   double omega, cv, K;    // 1/tau, C_v, K = 2 C_v - D
   float omegaf, cvf, Kf, inv2cvf;   // inv2cvf = 1 / (2 C_v)
   int npop;
+  int pr_on;              // Prandtl number != 1: quasi-equilibrium term of Eq. streaming_fg
+  double cpr;             // 1/tau - 1/tau_Pr, tau_Pr = (tau - 1/2)/Pr + 1/2
+  float cprf;
 };
 
 // ------------------------------------------------------------------------------------------
@@ -228,6 +231,7 @@ __device__ __forceinline__ T eq_em1(const EqFactors<T>& e, int a, int b) {
 // With X_k(a) = A_k(u_x) he[k][a] and S_m(b) = sum_{l=1..m} A_l(u_y) he[l][b] the equilibrium
 // deviation is f_ab^eq - w_ab = w_a w_b (drho + rho S_4(b)) + sum_k (rho w_a X_k(a)) (w_b (1 +
 // S_{4-k}(b))): after a per-vertex set-up of 45 factors, five FMAs per velocity.
+template <bool PR = false>
 __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Consts& cs,
                                                       const CollideK& cp) {
   // moments (Sec. II): rho = 1 + sum fbar, j = sum fbar xi, A2 = sum fbar |xi|^2, G = sum gbar.
@@ -261,6 +265,41 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
   const float rho = 1.f + drho;
   const float inv_rho = 1.f / rho;
   const float ux = jx * inv_rho, uy = jy * inv_rho;
+  // Pr != 1 (Sec. II.C): the non-equilibrium centred third moments of f and g, as (f, g) pairs
+  // xxx, xxy, xyy, yyy.  The equilibrium's centred third moment is zero, so they are those of the
+  // pre-collision populations: of the stored deviations plus the lattice-weight part,
+  // sum_i w_i (xi - u)^3 = -(u_a d_bc + u_b d_ac + u_c d_ab) - u_a u_b u_c (times K for g).
+  float2 Qn[4];
+  if constexpr (PR) {
+    float cx[kQ1], cy[kQ1];
+#pragma unroll
+    for (int a = 0; a < kQ1; ++a) {
+      cx[a] = cs.xif[a] - ux;
+      cy[a] = cs.xif[a] - uy;
+    }
+    float2 qxxx = make_float2(0.f, 0.f), qxxy = qxxx, qxyy = qxxx, qyyy = qxxx;
+#pragma unroll
+    for (int a = 0; a < kQ1; ++a) {
+      float2 s1 = make_float2(0.f, 0.f), s2 = s1;   // sum_b cy fg_ab, sum_b cy^2 fg_ab
+#pragma unroll
+      for (int b = 0; b < kQ1; ++b) {
+        s1 = fma2(bcast2(cy[b]), fg[5 * a + b], s1);
+        s2 = fma2(bcast2(cy[b] * cy[b]), fg[5 * a + b], s2);
+      }
+      const float cx2 = cx[a] * cx[a];
+      qxxx = fma2(bcast2(cx2 * cx[a]), rs[a], qxxx);
+      qxxy = fma2(bcast2(cx2), s1, qxxy);
+      qxyy = fma2(bcast2(cx[a]), s2, qxyy);
+      qyyy = fma2(bcast2(cy[a] * cy[a] * cy[a]), cl[a], qyyy);
+    }
+    const float wxxx = -3.f * ux - ux * ux * ux, wxxy = -uy - ux * ux * uy;
+    const float wxyy = -ux - ux * uy * uy, wyyy = -3.f * uy - uy * uy * uy;
+    Qn[0] = make_float2(qxxx.x + wxxx, qxxx.y + cp.Kf * wxxx);
+    Qn[1] = make_float2(qxxy.x + wxxy, qxxy.y + cp.Kf * wxxy);
+    Qn[2] = make_float2(qxyy.x + wxyy, qxyy.y + cp.Kf * wxyy);
+    Qn[3] = make_float2(qyyy.x + wyyy, qyyy.y + cp.Kf * wyyy);
+  }
+  (void)Qn;
   // theta - 1 = (A2 + G - rho |u|^2 - 2 C_v drho) / (2 C_v rho)
   const float q = (a2 + G - rho * (ux * ux + uy * uy) - 2.f * cp.cvf * drho) * inv_rho * cp.inv2cvf;
   float ax[5], ay[5];
@@ -371,6 +410,34 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
       if (a > 0) {
         fg[5 * (a + 2) + b].x -= ta * (cm * cs.wf[b] + r2w[b]);
         fg[5 * (a + 2) + b].y -= tg;
+      }
+    }
+  }
+  if constexpr (PR) {
+    // + (1/tau - 1/tau_Pr) f^qe with f^qe_ab = w_a w_b (Q_xxx h3(a) + Q_xxy h2(a) h1(b) +
+    // Q_xyy h1(a) h2(b) + Q_yyy h3(b)), h_n = He_n / n!: the contraction w_i Q : H^(3)(xi_i) / 3!
+    // of Sec. II.C written out over the tensor-product velocities (it carries no mass, momentum
+    // or energy); the same with g's moments for g
+    float wh1[kQ1], wh2[kQ1], wh3[kQ1];
+#pragma unroll
+    for (int b = 0; b < kQ1; ++b) {
+      wh1[b] = cs.wf[b] * cs.hef[1][b];
+      wh2[b] = cs.wf[b] * cs.hef[2][b];
+      wh3[b] = cs.wf[b] * cs.hef[3][b];
+    }
+#pragma unroll
+    for (int a = 0; a < kQ1; ++a) {
+      const float ca = cp.cprf * cs.wf[a];
+      const float2 B0 = __fmul2_rn(bcast2(ca * cs.hef[3][a]), Qn[0]);
+      const float2 B1 = __fmul2_rn(bcast2(ca * cs.hef[2][a]), Qn[1]);
+      const float2 B2 = __fmul2_rn(bcast2(ca * cs.hef[1][a]), Qn[2]);
+      const float2 B3 = __fmul2_rn(bcast2(ca), Qn[3]);
+#pragma unroll
+      for (int b = 0; b < kQ1; ++b) {
+        float2 t = fma2(bcast2(cs.wf[b]), B0, fg[5 * a + b]);
+        t = fma2(bcast2(wh1[b]), B1, t);
+        t = fma2(bcast2(wh2[b]), B2, t);
+        fg[5 * a + b] = fma2(bcast2(wh3[b]), B3, t);
       }
     }
   }

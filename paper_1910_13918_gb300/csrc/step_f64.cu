@@ -70,16 +70,45 @@ __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_consta
   eq_factors<double>(a.cs.he, ux, uy, q, e);
   const double om = a.cp.omega;
   const size_t o = (size_t)iy * a.pitch + (size_t)ix * a.xs;
+  // Pr != 1 (Sec. II.C): non-equilibrium centred third moments of f and g (xxx, xxy, xyy, yyy)
+  double qf[4] = {0.0, 0.0, 0.0, 0.0}, qg[4] = {0.0, 0.0, 0.0, 0.0};
+  if (a.cp.pr_on) {
+#pragma unroll 1
+    for (int i = 0; i < kQ; ++i) {
+      const int ia = i / 5, ib = i % 5;
+      const double feq = a.cs.w[ia] * a.cs.w[ib] * rho * (1.0 + eq_em1<double>(e, ia, ib));
+      const double df = f[i] - feq, dg = npop == 2 ? g[i] - a.cp.K * theta * feq : 0.0;
+      const double cx = a.cs.xi[ia] - ux, cy = a.cs.xi[ib] - uy;
+      const double m[4] = {cx * cx * cx, cx * cx * cy, cx * cy * cy, cy * cy * cy};
+      for (int k = 0; k < 4; ++k) {
+        qf[k] += df * m[k];
+        qg[k] += dg * m[k];
+      }
+    }
+  }
 #pragma unroll
   for (int ia = 0; ia < kQ1; ++ia)
 #pragma unroll
     for (int ib = 0; ib < kQ1; ++ib) {
       const int i = 5 * ia + ib;
       const double feq = a.cs.w[ia] * a.cs.w[ib] * rho * (1.0 + eq_em1<double>(e, ia, ib));
-      dst[(size_t)i * a.plane_stride + o] = f[i] - om * (f[i] - feq);
+      // quasi-equilibrium: w_a w_b (Q_xxx h3(a) + Q_xxy h2(a) h1(b) + Q_xyy h1(a) h2(b) + Q_yyy h3(b))
+      double sf = 0.0, sg = 0.0;
+      if (a.cp.pr_on) {
+        const double wab = a.cs.w[ia] * a.cs.w[ib];
+        const double h[4] = {a.cs.he[3][ia], a.cs.he[2][ia] * a.cs.he[1][ib],
+                             a.cs.he[1][ia] * a.cs.he[2][ib], a.cs.he[3][ib]};
+        for (int k = 0; k < 4; ++k) {
+          sf += qf[k] * h[k];
+          sg += qg[k] * h[k];
+        }
+        sf *= a.cp.cpr * wab;
+        sg *= a.cp.cpr * wab;
+      }
+      dst[(size_t)i * a.plane_stride + o] = f[i] - om * (f[i] - feq) + sf;
       if (npop == 2) {
         const double geq = a.cp.K * theta * feq;
-        dst[(size_t)i * a.plane_stride + a.ps + o] = g[i] - om * (g[i] - geq);
+        dst[(size_t)i * a.plane_stride + a.ps + o] = g[i] - om * (g[i] - geq) + sg;
       }
     }
   if (!(rho > 0.0 && theta > 0.0 && isfinite(rho) && isfinite(theta))) atomicOr(a.flag, 1);

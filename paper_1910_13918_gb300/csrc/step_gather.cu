@@ -10,7 +10,7 @@
 
 namespace sllbm {
 
-template <int P, typename Store, bool Mapped>
+template <int P, typename Store, bool Mapped, bool PR>
 __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant__ StepArgs a) {
   long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (a.vlist) {
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
     fg[i] = acc;
   }
   const bool two = a.cp.npop == 2;
-  const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
+  const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp);
   if (!ok) atomicOr(a.flag, 1);
   if (!two) {   // one population: the g slots stay zero
 #pragma unroll
@@ -81,26 +81,26 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
   });
 }
 
-template <int P, typename Store>
+template <int P, typename Store, bool PR>
 static cudaError_t launch_p(const StepArgs& a, cudaStream_t s) {
   const int threads = 128;
   const long long n = a.vlist ? a.nlist : a.nv;
   if (n == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
   if (a.mapped)
-    step_gather_kernel<P, Store, true><<<blocks, threads, 0, s>>>(a);
+    step_gather_kernel<P, Store, true, PR><<<blocks, threads, 0, s>>>(a);
   else
-    step_gather_kernel<P, Store, false><<<blocks, threads, 0, s>>>(a);
+    step_gather_kernel<P, Store, false, PR><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename Store>
 static cudaError_t launch_store(const StepArgs& a, cudaStream_t s) {
   switch (a.P) {
-    case 1: return launch_p<1, Store>(a, s);
-    case 2: return launch_p<2, Store>(a, s);
-    case 3: return launch_p<3, Store>(a, s);
-    case 4: return launch_p<4, Store>(a, s);
+    case 1: return a.cp.pr_on ? launch_p<1, Store, true>(a, s) : launch_p<1, Store, false>(a, s);
+    case 2: return a.cp.pr_on ? launch_p<2, Store, true>(a, s) : launch_p<2, Store, false>(a, s);
+    case 3: return a.cp.pr_on ? launch_p<3, Store, true>(a, s) : launch_p<3, Store, false>(a, s);
+    case 4: return a.cp.pr_on ? launch_p<4, Store, true>(a, s) : launch_p<4, Store, false>(a, s);
   }
   return cudaErrorInvalidValue;
 }

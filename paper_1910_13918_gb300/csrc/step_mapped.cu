@@ -54,7 +54,7 @@ __device__ __forceinline__ void tail_weights(const float (&wc)[4][5], float r, f
 
 }  // namespace
 
-template <int P, typename Store>
+template <int P, typename Store, bool PR>
 __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_constant__ MappedArgs ma) {
   constexpr int NSB = kMStages, PD = NSB - 1;
   const StepArgs& a = ma.a;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
         fg[5 * ph + b] = acc;
       }
     }
-    const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
+    const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp);
     if (store) {
       if (!ok) atomicOr(a.flag, 1);
       Store* dst = static_cast<Store*>(a.dst);
@@ -178,7 +178,7 @@ size_t mapped_smem_bytes(int bw, int bh, int store) {
   return 128 + (size_t)kMStages * (5 * st + 4 * kMDesc) + sizeof(uint64_t) * kMStages;
 }
 
-template <int P, typename Store>
+template <int P, typename Store, bool PR>
 static cudaError_t launch_p(const StepArgs& a, const MappedTables& t, cudaStream_t s) {
   if (a.xs != 2 || a.ps != 1) return cudaErrorNotSupported;   // interleaved (f, g) pairs only
   MappedArgs ma;
@@ -220,30 +220,30 @@ static cudaError_t launch_p(const StepArgs& a, const MappedTables& t, cudaStream
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   const size_t smem = mapped_smem_bytes(t.bw, t.bh, sizeof(Store) == 2 ? kStoreBF16 : kStoreF32);
-  cudaError_t e = cudaFuncSetAttribute(step_mapped_kernel<P, Store>,
+  cudaError_t e = cudaFuncSetAttribute(step_mapped_kernel<P, Store, PR>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(step_mapped_kernel<P, Store>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    e = cudaFuncSetAttribute(step_mapped_kernel<P, Store, PR>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   int dev = 0, n_sm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mapped_kernel<P, Store>, kMNT, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_mapped_kernel<P, Store, PR>, kMNT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int ntiles = ((a.nx + kMappedTileX - 1) / kMappedTileX) * ((a.ny + kMappedTileY - 1) / kMappedTileY);
   const int grid = ntiles < n_sm * per_sm ? ntiles : n_sm * per_sm;   // persistent CTAs
-  step_mapped_kernel<P, Store><<<grid, kMNT, smem, s>>>(ma);
+  step_mapped_kernel<P, Store, PR><<<grid, kMNT, smem, s>>>(ma);
   return cudaGetLastError();
 }
 
 template <typename Store>
 static cudaError_t launch_store(const StepArgs& a, const MappedTables& t, cudaStream_t s) {
   switch (a.P) {
-    case 1: return launch_p<1, Store>(a, t, s);
-    case 2: return launch_p<2, Store>(a, t, s);
-    case 3: return launch_p<3, Store>(a, t, s);
-    case 4: return launch_p<4, Store>(a, t, s);
+    case 1: return a.cp.pr_on ? launch_p<1, Store, true>(a, t, s) : launch_p<1, Store, false>(a, t, s);
+    case 2: return a.cp.pr_on ? launch_p<2, Store, true>(a, t, s) : launch_p<2, Store, false>(a, t, s);
+    case 3: return a.cp.pr_on ? launch_p<3, Store, true>(a, t, s) : launch_p<3, Store, false>(a, t, s);
+    case 4: return a.cp.pr_on ? launch_p<4, Store, true>(a, t, s) : launch_p<4, Store, false>(a, t, s);
   }
   return cudaErrorInvalidValue;
 }

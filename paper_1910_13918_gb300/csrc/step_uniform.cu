@@ -174,7 +174,7 @@ struct UniformArgs {
   int gx, gy;                            // ghost columns / rows before the interior origin
 };
 
-template <int P, typename Store, bool Tall>
+template <int P, typename Store, bool Tall, bool PR>
 __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MINB)
     step_uniform_kernel(const __grid_constant__ UniformArgs<P> ua) {
   using TS = TileShape<P, Tall>;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
       if (j != 0) continue;
 
       // ---- the tile of the x pass is complete: collide and store ----
-      const bool ok = collide_deviation_f32(fg, a.cs, a.cp);
+      const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp);
       if (x < a.nx && y < a.ny && ua.std_x[x] && ua.std_y[y]) {
         if (!ok) atomicOr(a.flag, 1);
         Store* dst = static_cast<Store*>(a.dst);
@@ -318,7 +318,7 @@ static size_t smem_bytes() {
          sizeof(float2) * 2 * kQ1 * P * 4 + sizeof(int) * table_ints(P) + sizeof(uint64_t) * kStageBuffers;
 }
 
-template <int P, typename Store, bool Tall>
+template <int P, typename Store, bool Tall, bool PR>
 static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStream_t s) {
   using TS = TileShape<P, Tall>;
   if (a.xs != 2 || a.ps != 1) return cudaErrorNotSupported;   // interleaved (f, g) pairs only
@@ -366,10 +366,10 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
   const size_t smem = smem_bytes<P, Store, Tall>();
   static bool configured = false;  // per template instance
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, Tall>,
+    cudaError_t e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, Tall, PR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)   // all of the unified L1/shared storage as shared memory
-      e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, Tall>,
+      e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, Tall, PR>,
                                cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     configured = true;
@@ -383,17 +383,18 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
   }
   const int ntiles = ((a.nx + 31) / 32) * ((a.ny + TS::TY - 1) / TS::TY);
   const int grid = ntiles < n_sm * TS::MINB ? ntiles : n_sm * TS::MINB;   // persistent CTAs
-  step_uniform_kernel<P, Store, Tall><<<grid, TS::NT, smem, s>>>(ua);
+  step_uniform_kernel<P, Store, Tall, PR><<<grid, TS::NT, smem, s>>>(ua);
   return cudaGetLastError();
 }
 
 template <typename Store, bool Tall>
 static cudaError_t launch_store(const StepArgs& a, const UniformTables& t, cudaStream_t s) {
   switch (a.P) {
-    case 1: return launch_p<1, Store, Tall>(a, t, s);
-    case 2: return launch_p<2, Store, Tall>(a, t, s);
-    case 3: return launch_p<3, Store, Tall>(a, t, s);
-    case 4: return launch_p<4, Store, Tall>(a, t, s);
+    // Pr != 1 runs in the default (short) tile only
+    case 1: return a.cp.pr_on ? launch_p<1, Store, false, true>(a, t, s) : launch_p<1, Store, Tall, false>(a, t, s);
+    case 2: return a.cp.pr_on ? launch_p<2, Store, false, true>(a, t, s) : launch_p<2, Store, Tall, false>(a, t, s);
+    case 3: return a.cp.pr_on ? launch_p<3, Store, false, true>(a, t, s) : launch_p<3, Store, Tall, false>(a, t, s);
+    case 4: return a.cp.pr_on ? launch_p<4, Store, false, true>(a, t, s) : launch_p<4, Store, Tall, false>(a, t, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -40,7 +40,8 @@ class GridDesc(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("velset", ctypes.c_int), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
-                ("cv", ctypes.c_double), ("T0", ctypes.c_double), ("prec", ctypes.c_int)]
+                ("cv", ctypes.c_double), ("T0", ctypes.c_double), ("prec", ctypes.c_int),
+                ("pr", ctypes.c_double)]
 
 
 class SLLBMError(RuntimeError):
@@ -106,7 +107,8 @@ class SLLBM:
     """
 
     def __init__(self, *, nx_cells, ny_cells, order, x0, x1, y0, y1, bc_x, bc_y, dt, tau, cv,
-                 prec="f32", nodes=NODES_GLC, map_kind=MAP_IDENTITY, map_a=0.0, stream=None):
+                 prec="f32", nodes=NODES_GLC, map_kind=MAP_IDENTITY, map_a=0.0, pr=1.0,
+                 stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("SLLBM needs a CUDA device; there is no CPU path")
@@ -115,7 +117,7 @@ class SLLBM:
         self.prec = prec
         g = GridDesc(nx_cells, ny_cells, order, x0, x1, y0, y1, bc_x, bc_y, nodes, map_kind,
                      (ctypes.c_double * 4)(map_a, 0.0, 0.0, 0.0))
-        p = Params(0, dt, tau, cv, 1.0, PRECISIONS[prec])
+        p = Params(0, dt, tau, cv, 1.0, PRECISIONS[prec], pr)
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         self._check(self.lib.sllbm_create(ctypes.byref(g), ctypes.byref(p),
@@ -134,7 +136,8 @@ class SLLBM:
         return cls(nx_cells=w.nx_cells, ny_cells=w.ny_cells, order=w.order, x0=w.x0, x1=w.x1,
                    y0=w.y0, y1=w.y1, bc_x=w.bc_x, bc_y=w.bc_y, dt=w.dt, tau=w.tau, cv=w.cv,
                    prec=prec, nodes=NODES_GLC if w.nodes == "glc" else NODES_EQUIDISTANT,
-                   map_kind=MAP_SINE if w.map_a else MAP_IDENTITY, map_a=w.map_a, stream=stream)
+                   map_kind=MAP_SINE if w.map_a else MAP_IDENTITY, map_a=w.map_a, pr=w.pr,
+                   stream=stream)
 
     # -- plumbing -------------------------------------------------------------------------------
     def _check(self, status, ctx="self"):
