@@ -82,12 +82,16 @@ typedef struct {
  * Prandtl number pr (Sec. II.C, Eq. streaming_fg): 1 (or 0, which reads as 1) is plain BGK;
  * any other positive value adds (1/tau - 1/tau_Pr) f^qe, tau_Pr = (tau - 1/2)/Pr + 1/2, with the
  * quasi-equilibrium f^qe_i = w_i Q^neq : H^(3)(xi_i) / 3! of the non-equilibrium centred third
- * moment (and the same projection of g's own for g).  The adjoint covers Pr = 1 only. */
+ * moment (and the same projection of g's own for g).  The adjoint covers Pr = 1 only.
+ * isothermal = 1 evaluates the equilibrium at theta = 1 (the isothermal configuration of the
+ * moving Taylor-Green vortex, Sec. III.A): mass and momentum are conserved, energy is not; it
+ * requires cv = 1 (one population). */
 typedef struct {
     int velset;                 /* sllbm_velset */
     double dt, tau, cv, T0;
     int prec;                   /* sllbm_prec   */
     double pr;                  /* Prandtl number; 0 or 1: plain BGK */
+    int isothermal;             /* 1: equilibrium at theta = 1 (Sec. III.A); needs cv = 1 */
 } sllbm_params;
 
 typedef struct sllbm_ctx sllbm_ctx;  /* opaque, library-owned */
@@ -160,7 +164,7 @@ sllbm_status sllbm_set_state(sllbm_ctx* ctx, const void* src_dev);
  * [4][ny][nx] FP32 = (rho, u, v, theta) -- exactly what sllbm_moments returns for the state the
  * step produced.  S^T is applied as a gather (pull) over precomputed transposed stencils: no
  * atomics, deterministic.  Works in every precision mode (FP32 arithmetic); a context with
- * Pr != 1 gets SLLBM_ERR_UNSUPPORTED. */
+ * Pr != 1 or the isothermal equilibrium gets SLLBM_ERR_UNSUPPORTED. */
 sllbm_status sllbm_adjoint_step(sllbm_ctx* ctx, const float* lambda_in_dev, float* lambda_out_dev,
                                 const float* saved_moments_dev);
 

@@ -223,13 +223,16 @@ def tau_prandtl(tau, pr):
     return (tau - 0.5) / pr + 0.5
 
 
-def collide(f, g, tau, cv, pr=1.0):
+def collide(f, g, tau, cv, pr=1.0, isothermal=False):
     """Collision at the vertices (Eq. streaming_fg):
     f* = f - (f - f^eq)/tau + (1/tau - 1/tau_Pr) f^qe, the same for g with g^eq = (2 C_v - D) theta
     f^eq, where f^qe (g^qe) is the quasi-equilibrium of the non-equilibrium centred third moment
     of f (of g).  With Pr = 1, tau_Pr = tau and the quasi-equilibrium term is zero: plain BGK.
+    ``isothermal``: the equilibrium at theta = 1 (the isothermal configuration of Sec. III.A).
     """
     rho, u, theta = macroscopic(f, g, cv)
+    if isothermal:
+        theta = np.ones_like(theta)
     feq = equilibrium_f(rho, u, theta)
     geq = (2.0 * cv - D) * theta * feq
     fn, gn = f - (f - feq) / tau, g - (g - geq) / tau
@@ -471,16 +474,16 @@ def stream(F, dep: Departures):
     return out
 
 
-def step(f, g, dep: Departures, tau, cv, pr=1.0):
+def step(f, g, dep: Departures, tau, cv, pr=1.0, isothermal=False):
     """One SLLBM time step: pull the post-collision populations, then collide at every vertex."""
     fpre = stream(f, dep)
     gpre = stream(g, dep)
-    return collide(fpre, gpre, tau, cv, pr)
+    return collide(fpre, gpre, tau, cv, pr, isothermal)
 
 
-def run(f, g, dep: Departures, tau, cv, nsteps, pr=1.0):
+def run(f, g, dep: Departures, tau, cv, nsteps, pr=1.0, isothermal=False):
     for _ in range(nsteps):
-        f, g = step(f, g, dep, tau, cv, pr)
+        f, g = step(f, g, dep, tau, cv, pr, isothermal)
     return f, g
 
 

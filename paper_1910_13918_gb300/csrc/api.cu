@@ -548,6 +548,7 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
     return SLLBM_ERR_ARG;
   if (!(p->dt > 0.0) || !(p->tau > 0.5) || !(p->cv >= 1.0) || p->T0 != 1.0) return SLLBM_ERR_ARG;
   if (!(p->pr >= 0.0) || !(p->pr < 1e6)) return SLLBM_ERR_ARG;   // NaN, negative or absurd
+  if (p->isothermal != 0 && (p->isothermal != 1 || p->cv != 1.0)) return SLLBM_ERR_ARG;
   if ((long long)g->nx_cells * g->order > (1 << 20) || (long long)g->ny_cells * g->order > (1 << 20))
     return SLLBM_ERR_UNSUPPORTED;
   sllbm_ctx* c = new (std::nothrow) sllbm_ctx();
@@ -573,6 +574,7 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   c->cp.Kf = (float)c->cp.K;
   c->cp.inv2cvf = (float)(0.5 / p->cv);
   c->cp.npop = c->npop;
+  c->cp.iso = p->isothermal;
   {
     const double pr = (p->pr == 0.0) ? 1.0 : p->pr;
     const double tau_pr = (p->tau - 0.5) / pr + 0.5;
@@ -980,7 +982,8 @@ static sllbm_status build_mapped_transpose(sllbm_ctx* c) {
 sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_out, const float* moments) {
   if (!c || !lam_in || !lam_out || !moments) return fail(c, SLLBM_ERR_ARG, "null pointer");
   if (lam_in == lam_out) return fail(c, SLLBM_ERR_ARG, "lambda_in and lambda_out alias");
-  if (c->cp.pr_on) return fail(c, SLLBM_ERR_UNSUPPORTED, "the adjoint covers Prandtl number 1 only");
+  if (c->cp.pr_on || c->cp.iso)
+    return fail(c, SLLBM_ERR_UNSUPPORTED, "the adjoint covers the thermal BGK collision (Pr = 1) only");
   if (!c->precomputed) return fail(c, SLLBM_ERR_STATE, "precompute_departures first");
   const bool mapped = c->map.kind != SLLBM_MAP_IDENTITY;
   if (!c->transposed) {

@@ -43,6 +43,7 @@ struct CollideK {
   double omega, cv, K;    // 1/tau, C_v, K = 2 C_v - D
   float omegaf, cvf, Kf, inv2cvf;   // inv2cvf = 1 / (2 C_v)
   int npop;
+  int iso;                // isothermal: equilibrium at theta = 1, energy not conserved
   int pr_on;              // Prandtl number != 1: quasi-equilibrium term of Eq. streaming_fg
   double cpr;             // 1/tau - 1/tau_Pr, tau_Pr = (tau - 1/2)/Pr + 1/2
   float cprf;
@@ -301,7 +302,8 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
   }
   (void)Qn;
   // theta - 1 = (A2 + G - rho |u|^2 - 2 C_v drho) / (2 C_v rho)
-  const float q = (a2 + G - rho * (ux * ux + uy * uy) - 2.f * cp.cvf * drho) * inv_rho * cp.inv2cvf;
+  const float q = cp.iso ? 0.f
+                        : (a2 + G - rho * (ux * ux + uy * uy) - 2.f * cp.cvf * drho) * inv_rho * cp.inv2cvf;
   float ax[5], ay[5];
   ax[1] = ux;
   ax[2] = ux * ux + q;
@@ -441,7 +443,7 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
       }
     }
   }
-  if (cp.npop != 2) {
+  if (cp.npop != 2 && !cp.iso) {
     // single population: remove the energy residual along w (|xi|^2 - 2), which carries no
     // mass or momentum; its energy is sum w |xi|^4 - 2 sum w |xi|^2 = 8 - 4 = 4
     const float c = 0.25f * c3;

@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_consta
     e2 += f[i] * (cx * cx + cy * cy) + (npop == 2 ? g[i] : 0.0);
   }
   const double ux = jx / rho, uy = jy / rho;
-  const double theta = (e2 - rho * (ux * ux + uy * uy)) / (2.0 * a.cp.cv * rho);
+  const double theta = a.cp.iso ? 1.0 : (e2 - rho * (ux * ux + uy * uy)) / (2.0 * a.cp.cv * rho);
   const double q = theta - 1.0;
   EqFactors<double> e;
   eq_factors<double>(a.cs.he, ux, uy, q, e);

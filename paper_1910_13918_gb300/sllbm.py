@@ -41,7 +41,7 @@ class GridDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("velset", ctypes.c_int), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
                 ("cv", ctypes.c_double), ("T0", ctypes.c_double), ("prec", ctypes.c_int),
-                ("pr", ctypes.c_double)]
+                ("pr", ctypes.c_double), ("isothermal", ctypes.c_int)]
 
 
 class SLLBMError(RuntimeError):
@@ -108,7 +108,7 @@ class SLLBM:
 
     def __init__(self, *, nx_cells, ny_cells, order, x0, x1, y0, y1, bc_x, bc_y, dt, tau, cv,
                  prec="f32", nodes=NODES_GLC, map_kind=MAP_IDENTITY, map_a=0.0, pr=1.0,
-                 stream=None):
+                 isothermal=False, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("SLLBM needs a CUDA device; there is no CPU path")
@@ -117,7 +117,7 @@ class SLLBM:
         self.prec = prec
         g = GridDesc(nx_cells, ny_cells, order, x0, x1, y0, y1, bc_x, bc_y, nodes, map_kind,
                      (ctypes.c_double * 4)(map_a, 0.0, 0.0, 0.0))
-        p = Params(0, dt, tau, cv, 1.0, PRECISIONS[prec], pr)
+        p = Params(0, dt, tau, cv, 1.0, PRECISIONS[prec], pr, int(bool(isothermal)))
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         self._check(self.lib.sllbm_create(ctypes.byref(g), ctypes.byref(p),
@@ -137,7 +137,7 @@ class SLLBM:
                    y0=w.y0, y1=w.y1, bc_x=w.bc_x, bc_y=w.bc_y, dt=w.dt, tau=w.tau, cv=w.cv,
                    prec=prec, nodes=NODES_GLC if w.nodes == "glc" else NODES_EQUIDISTANT,
                    map_kind=MAP_SINE if w.map_a else MAP_IDENTITY, map_a=w.map_a, pr=w.pr,
-                   stream=stream)
+                   isothermal=w.isothermal, stream=stream)
 
     # -- plumbing -------------------------------------------------------------------------------
     def _check(self, status, ctx="self"):

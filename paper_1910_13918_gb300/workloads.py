@@ -53,6 +53,7 @@ class Workload:
     map_a: float = 0.0             # sine-map amplitude (0: uniform grid)
     cv: float = CV
     pr: float = 1.0                # Prandtl number (1: plain BGK, Sec. II.C)
+    isothermal: bool = False       # theta = 1 in the equilibrium (Sec. III.A); needs cv = 1
     nodes: str = "glc"
     seed: int = 0
     extra: dict = dataclasses.field(default_factory=dict)
@@ -92,6 +93,8 @@ class Workload:
             return self.extra["Ma_A"]
         if self.kind == "sdp":
             return self.extra["U"]
+        if self.kind == "tgvm":
+            return self.extra["u_v"]
         return 1.0
 
     def fields(self, x, y, perturb=False):
@@ -228,7 +231,26 @@ def sdp_density(w: Workload, x, y, t):
     return 1.0 + 0.2 * np.sin(np.pi * (x - w.extra["U"] * t)) * np.sin(np.pi * y)
 
 
-_GENERATORS = {"tgv": _tgv, "sod": _sod, "riemann": _riemann, "svi": _svi, "sdp": _sdp}
+def _tgvm(w, x, y):
+    u, v, rho = tgvm_reference(w, x, y, 0.0)
+    return rho, u, v, np.ones_like(x)
+
+
+def tgvm_reference(w: Workload, x, y, t):
+    """Moving Taylor-Green vortex (Sec. III.A) at lattice time t: velocity (u, v) and density
+    rho = 1 + p' (isothermal, c_s = 1), the vortex carried along x with u_h and decaying with
+    exp(-2 nu t)."""
+    uv, uh, nu = w.extra["u_v"], w.extra["u_h"], w.extra["nu"]
+    xs = x - uh * t
+    d = np.exp(-2.0 * nu * t)
+    u = uh + uv * np.sin(xs) * np.cos(y) * d
+    v = -uv * np.cos(xs) * np.sin(y) * d
+    rho = 1.0 + uv ** 2 / 4.0 * (np.cos(2.0 * xs) + np.cos(2.0 * y)) * d * d
+    return u, v, rho
+
+
+_GENERATORS = {"tgv": _tgv, "sod": _sod, "riemann": _riemann, "svi": _svi, "sdp": _sdp,
+               "tgvm": _tgvm}
 
 
 def svi_envelope(w: Workload, x, y):
@@ -325,6 +347,24 @@ def svi_pr():
     return w
 
 
+def tgv_moving(points=32, ma_h=0.05):
+    """Isothermal moving Taylor-Green vortex (Sec. III.A) on [0, 2 pi]^2, p = 4, points x points
+    vertices: Ma_v = 0.01 (u_v = 0.01, c_s = 1), horizontal Mach number Ma_h, Re = u_v 2 pi / nu
+    = 10, compared at the time the vortex speed has decayed to 0.1 u_v.  The paper's time steps
+    (0.0008 at 16 points, halved per refinement) are in its unit of time, where u_v = 1: in
+    lattice units dt = 0.0008 / u_v = 0.08 at 16 points, and the end time 1.83 is 183."""
+    uv = 0.01
+    nu = uv * 2.0 * math.pi / 10.0
+    t_end = math.log(10.0) / (2.0 * nu)          # exp(-2 nu t) = 0.1
+    steps0 = int(round(t_end / 0.08))
+    steps = steps0 * (points // 16)
+    dt = t_end / steps
+    L = 2.0 * math.pi
+    return Workload(f"tgvm{points}_p4_mah{ma_h:g}", points // 4, points // 4, 4, 0.0, L, 0.0, L,
+                    PERIODIC, PERIODIC, dt, nu / dt + 0.5, steps, "tgvm", cv=1.0, isothermal=True,
+                    seed=8, extra={"u_v": uv, "u_h": ma_h, "nu": nu, "t_end": t_end})
+
+
 def sdp(points=16, step_factor=1):
     """Smooth density propagation (Sec. III.B, Table II) on [-1,1]^2, periodic, p = 4, with
     points x points vertices (points / 4 cells per axis).
@@ -344,4 +384,5 @@ def sdp(points=16, step_factor=1):
 
 
 ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
-       "riemann_paper": riemann_paper, "svi": svi, "svi_pr": svi_pr, "sdp": sdp}
+       "riemann_paper": riemann_paper, "svi": svi, "svi_pr": svi_pr, "sdp": sdp,
+       "tgv_moving": tgv_moving}

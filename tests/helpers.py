@@ -24,7 +24,7 @@ def oracle_state(w: W.Workload, nsteps, perturb=True):
     grid = oracle_grid(w)
     X, Y = grid.coords()
     f, g = o.initial_state(*w.fields(X, Y, perturb=perturb), w.cv)
-    return o.run(f, g, o.Departures(grid, w.dt), w.tau, w.cv, nsteps, w.pr)
+    return o.run(f, g, o.Departures(grid, w.dt), w.tau, w.cv, nsteps, w.pr, w.isothermal)
 
 
 def oracle_run(w: W.Workload, nsteps, perturb=True):
@@ -77,7 +77,7 @@ def oracle_step_at(w: W.Workload, vertices, perturb=True):
     f0, g0 = o.initial_state(*sub, w.cv)
     fpre = o.stream(SparseField(grid.nx, keys, f0), dep)
     gpre = o.stream(SparseField(grid.nx, keys, g0), dep)
-    f1, g1 = o.collide(fpre, gpre, w.tau, w.cv, w.pr)
+    f1, g1 = o.collide(fpre, gpre, w.tau, w.cv, w.pr, w.isothermal)
     rho, u, th = o.macroscopic(f1, g1, w.cv)
     return rho, u[..., 0], u[..., 1], th
 

@@ -1,4 +1,4 @@
-"""Pins of the oracle's variable-Prandtl collision (Sec. II.C, Eq. streaming_fg).
+"""Pins of the oracle's variable-Prandtl and isothermal collisions (Sec. II.C, Sec. III.A).
 
 The quasi-equilibrium exists to relax the heat flux with its own time tau_Pr = (tau - 1/2)/Pr +
 1/2 while everything else keeps tau.  Written out, for a collision at one vertex (u is unchanged,
@@ -84,3 +84,20 @@ def test_equilibrium_has_no_centred_heat_flux():
     theta = 0.7 + 0.6 * rng.random(5)
     feq = o.equilibrium_f(rho, u, theta)
     assert np.max(np.abs(o.centered_third_moment(feq, u))) < 1e-14
+
+
+def test_isothermal_collision_relaxes_kinetic_temperature_to_one():
+    """The isothermal configuration (Sec. III.A, one population, C_v = 1): the equilibrium is
+    taken at theta = 1, so mass and momentum are kept while the kinetic temperature
+    (sum f |xi|^2 - rho |u|^2) / (2 rho) relaxes toward 1 by 1 - 1/tau."""
+    f, _, _ = _state(5)
+    g = np.zeros_like(f)
+    tau = 0.8
+    rho, u, theta = o.macroscopic(f, g, 1.0)
+    fn, gn = o.collide(f, g, tau, 1.0, isothermal=True)
+    rho2, u2, theta2 = o.macroscopic(fn, gn, 1.0)
+    np.testing.assert_allclose(rho2, rho, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(u2, u, rtol=0, atol=1e-14)
+    assert np.max(np.abs(theta - 1.0)) > 1e-2
+    np.testing.assert_allclose(theta2 - 1.0, (1 - 1 / tau) * (theta - 1.0), rtol=0, atol=1e-13)
+    assert np.max(np.abs(gn)) == 0.0
