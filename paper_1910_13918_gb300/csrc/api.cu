@@ -16,6 +16,7 @@
 using namespace sllbm;
 
 enum StepKernel { kKernelUniform = 0, kKernelGather = 1, kKernelPlainF64 = 2, kKernelMapped = 3 };
+constexpr int kXferChunks = 5;   // host transfers move the state in this many plane groups
 
 struct sllbm_ctx {
   sllbm_grid_desc g;
@@ -30,6 +31,8 @@ struct sllbm_ctx {
   size_t plane_stride = 0;
   ptrdiff_t ps = 0;
   void* dense = nullptr;                 // dense staging state for host transfers (on demand)
+  cudaStream_t xfer = nullptr;           // copy stream of the host transfers (on demand)
+  cudaEvent_t xev[kXferChunks + 1] = {};
   AxisK ax{}, ay{};
   MapK map{};
   Consts cs{};
@@ -467,17 +470,20 @@ static sllbm_status build_mapped_tiles(sllbm_ctx* c) {
 }
 
 // Dense [npop][25][ny][nx] <-> the internal layout.  Host transfers go through the dense staging
-// buffer (one contiguous copy) and the conversion kernel.
-static cudaError_t convert_state(sllbm_ctx* c, const void* src, void* dst, bool to_internal) {
-  return launch_state_convert(src, dst, to_internal, c->elem, c->npop, c->nx, c->ny, c->pitch,
+// buffer and the conversion kernel in kXferChunks plane groups: the copy of one group (on the
+// context's copy stream) overlaps the conversion of the previous one (on its compute stream).
+static cudaError_t convert_state(sllbm_ctx* c, const void* src, void* dst, bool to_internal,
+                                 int plane0, int nplanes) {
+  return launch_state_convert(src, dst, to_internal, c->elem, plane0, nplanes, c->nx, c->ny, c->pitch,
                               c->plane_stride, c->xs, c->ps, c->stream);
 }
 
 static size_t dense_bytes(const sllbm_ctx* c) { return (size_t)c->npop * kQ * c->nv * c->elem; }
 
 static sllbm_status copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
+  const int planes = c->npop * kQ;
   if (kind == cudaMemcpyDeviceToDevice) {
-    CUDA_TRY(c, convert_state(c, src, dst, to_internal));
+    CUDA_TRY(c, convert_state(c, src, dst, to_internal, 0, planes));
     return SLLBM_OK;
   }
   if (!c->dense) {
@@ -485,13 +491,41 @@ static sllbm_status copy_state(sllbm_ctx* c, void* dst, const void* src, bool to
     TRY(dalloc(c, &p, dense_bytes(c)));
     c->dense = p;
   }
-  if (to_internal) {
-    CUDA_TRY(c, cudaMemcpyAsync(c->dense, src, dense_bytes(c), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, convert_state(c, c->dense, dst, true));
-  } else {
-    CUDA_TRY(c, convert_state(c, src, c->dense, false));
-    CUDA_TRY(c, cudaMemcpyAsync(dst, c->dense, dense_bytes(c), cudaMemcpyDeviceToHost, c->stream));
+  if (!c->xfer) {
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->xfer, cudaStreamNonBlocking));
+    for (int k = 0; k <= kXferChunks; ++k) CUDA_TRY(c, cudaEventCreateWithFlags(&c->xev[k], cudaEventDisableTiming));
   }
+  const size_t plane_bytes = (size_t)c->nv * c->elem;
+  auto chunk = [&](int k, int* p0, int* np) {
+    *p0 = planes * k / kXferChunks;
+    *np = planes * (k + 1) / kXferChunks - *p0;
+  };
+  // the copy stream starts after the work already queued on the compute stream
+  CUDA_TRY(c, cudaEventRecord(c->xev[kXferChunks], c->stream));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->xfer, c->xev[kXferChunks], 0));
+  char* dense = static_cast<char*>(c->dense);
+  for (int k = 0; k < kXferChunks; ++k) {
+    int p0, np;
+    chunk(k, &p0, &np);
+    if (np == 0) continue;
+    if (to_internal) {
+      CUDA_TRY(c, cudaMemcpyAsync(dense + p0 * plane_bytes, static_cast<const char*>(src) + p0 * plane_bytes,
+                                  np * plane_bytes, cudaMemcpyHostToDevice, c->xfer));
+      CUDA_TRY(c, cudaEventRecord(c->xev[k], c->xfer));
+      CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->xev[k], 0));
+      CUDA_TRY(c, convert_state(c, dense, dst, true, p0, np));
+    } else {
+      CUDA_TRY(c, convert_state(c, src, dense, false, p0, np));
+      CUDA_TRY(c, cudaEventRecord(c->xev[k], c->stream));
+      CUDA_TRY(c, cudaStreamWaitEvent(c->xfer, c->xev[k], 0));
+      CUDA_TRY(c, cudaMemcpyAsync(static_cast<char*>(dst) + p0 * plane_bytes, dense + p0 * plane_bytes,
+                                  np * plane_bytes, cudaMemcpyDeviceToHost, c->xfer));
+    }
+  }
+  // the compute stream resumes after the last copy (so that synchronising it covers the transfer,
+  // and the staging buffer is not reused before the copies out of it are done)
+  CUDA_TRY(c, cudaEventRecord(c->xev[kXferChunks], c->xfer));
+  CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->xev[kXferChunks], 0));
   return SLLBM_OK;
 }
 
@@ -528,6 +562,12 @@ const char* sllbm_last_error(const sllbm_ctx* c) { return c ? c->err.c_str() : "
 
 sllbm_status sllbm_destroy(sllbm_ctx* c) {
   if (!c) return SLLBM_ERR_ARG;
+  if (c->xfer) {
+    cudaStreamSynchronize(c->xfer);
+    cudaStreamDestroy(c->xfer);
+    for (int k = 0; k <= kXferChunks; ++k)
+      if (c->xev[k]) cudaEventDestroy(c->xev[k]);
+  }
   for (void* p : c->allocations) cudaFree(p);
   delete c;
   return SLLBM_OK;

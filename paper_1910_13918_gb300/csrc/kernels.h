@@ -120,9 +120,10 @@ struct InitArgs {
   int store;
 };
 cudaError_t launch_init_equilibrium(const InitArgs& a, cudaStream_t s);
-// Dense [npop][25][ny][nx] <-> internal layout (interior origin `internal`), element size `elem`.
-cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int npop,
-                                 int nx, int ny, int pitch, size_t plane_stride, int xs,
+// Dense [npop][25][ny][nx] <-> internal layout (interior origin `internal`), element size `elem`,
+// for the dense planes [plane0, plane0 + nplanes) (plane = pop * 25 + velocity).
+cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int plane0,
+                                 int nplanes, int nx, int ny, int pitch, size_t plane_stride, int xs,
                                  ptrdiff_t ps, cudaStream_t s);
 // Copy the periodic images of interior vertices into the ghost cells of `planes` planes (clamped
 // copies on non-periodic axes).  `origin`: interior origin of plane 0; elem: bytes per element.

@@ -323,11 +323,12 @@ cudaError_t launch_ghost_fill(void* origin, int elem, size_t plane_stride, int p
 // Dense [npop][25][ny][nx] <-> internal layout (ghost cells, row pitch, interleaved pairs).
 // ------------------------------------------------------------------------------------------
 template <typename E>
-__global__ void state_convert_kernel(const E* src, E* dst, int to_internal, int npop, int nx, int ny,
-                                     int pitch, size_t plane_stride, int xs, ptrdiff_t ps) {
+__global__ void state_convert_kernel(const E* src, E* dst, int to_internal, int plane0, int nplanes,
+                                     int nx, int ny, int pitch, size_t plane_stride, int xs, ptrdiff_t ps) {
   const long long nv = (long long)nx * ny;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)npop * kQ * nv) return;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 >= (long long)nplanes * nv) return;
+  const long long t = t0 + (long long)plane0 * nv;   // index in the dense layout
   const long long pl = t / nv, v = t - pl * nv;
   const int pop = (int)(pl / kQ), i = (int)(pl - (long long)pop * kQ);
   const int x = (int)(v % nx), y = (int)(v / nx);
@@ -338,10 +339,10 @@ __global__ void state_convert_kernel(const E* src, E* dst, int to_internal, int 
     dst[t] = src[o];
 }
 
-cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int npop,
-                                 int nx, int ny, int pitch, size_t plane_stride, int xs,
+cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int plane0,
+                                 int nplanes, int nx, int ny, int pitch, size_t plane_stride, int xs,
                                  ptrdiff_t ps, cudaStream_t s) {
-  const long long n = (long long)npop * kQ * nx * ny;
+  const long long n = (long long)nplanes * nx * ny;
   if (n == 0) return cudaSuccess;
   const int threads = 256;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
@@ -349,15 +350,15 @@ cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, i
   switch (elem) {
     case 2:
       state_convert_kernel<uint16_t><<<blocks, threads, 0, s>>>(static_cast<const uint16_t*>(src),
-          static_cast<uint16_t*>(dst), ti, npop, nx, ny, pitch, plane_stride, xs, ps);
+          static_cast<uint16_t*>(dst), ti, plane0, nplanes, nx, ny, pitch, plane_stride, xs, ps);
       break;
     case 4:
       state_convert_kernel<uint32_t><<<blocks, threads, 0, s>>>(static_cast<const uint32_t*>(src),
-          static_cast<uint32_t*>(dst), ti, npop, nx, ny, pitch, plane_stride, xs, ps);
+          static_cast<uint32_t*>(dst), ti, plane0, nplanes, nx, ny, pitch, plane_stride, xs, ps);
       break;
     case 8:
       state_convert_kernel<uint64_t><<<blocks, threads, 0, s>>>(static_cast<const uint64_t*>(src),
-          static_cast<uint64_t*>(dst), ti, npop, nx, ny, pitch, plane_stride, xs, ps);
+          static_cast<uint64_t*>(dst), ti, plane0, nplanes, nx, ny, pitch, plane_stride, xs, ps);
       break;
     default: return cudaErrorInvalidValue;
   }
