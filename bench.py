@@ -254,6 +254,31 @@ def run_ours(args):
     ms_max = max_over_ranks(ms)
     ms_step = ms_max / args.steps
     updates = w.updates_per_step
+
+    # adjoint step (Pr = 1, thermal collision): lambda' -> S^T J_C^T lambda' on the library's
+    # stream, at the moments of the state the forward run ended in; not part of `value`
+    adjoint = None
+    if not args.no_adjoint and not w.isothermal and w.pr == 1.0:
+        with torch.cuda.stream(stream):
+            mom = torch.stack([m["rho"], m["u"], m["v"], m["T"]]).contiguous()
+            gen = torch.Generator(device="cuda").manual_seed(7)
+            lam = torch.randn((2, 25, s.ny, s.nx), device="cuda", generator=gen)
+            out = torch.empty_like(lam)
+            for _ in range(3):
+                s.adjoint_step(lam, out, mom)
+            ka = 20
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(ka):
+                s.adjoint_step(lam, out, mom)
+                lam, out = out, lam
+            a1.record(stream)
+            torch.cuda.synchronize()
+        ms_adj = max_over_ranks(a0.elapsed_time(a1)) / ka
+        adjoint = {"ms_per_step": ms_adj, "value": updates * ws / (ms_adj * 1e-3) / 1e9, "unit": UNIT,
+                   "steps": ka, "launches_per_step": 2,
+                   "note": "sllbm_adjoint_step: pointwise J_C^T, then S^T as a pull over transposed stencils"}
     value = updates * args.steps * ws / (ms_max * 1e-3) / 1e9
 
     # end to end through the host-buffer entry point: copy state in, one step, copy state out
@@ -304,6 +329,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": clocks,
             "e2e": e2e,
+            "adjoint": adjoint,
             "gpu_launches": args.steps * s.launches_per_step,
             "mass_after": m["mass"],
         }
@@ -324,6 +350,7 @@ def main():
     ap.add_argument("--workload", default="tgv256")
     ap.add_argument("--prec", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

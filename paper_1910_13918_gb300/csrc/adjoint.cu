@@ -120,55 +120,103 @@ __global__ void __launch_bounds__(128) adjoint_collide_kernel(const __grid_const
   for (int i = 0; i < kQ; ++i) {
     const float cx = a.cs.xif[i / 5], cy = a.cs.xif[i % 5];
     const float lf = a.lam_in[(size_t)i * a.nv + v];
-    a.mu[(size_t)i * a.nv + v] = (1.f - om) * lf + om * (z0 + z1 * cx + z2 * cy + z3 * (cx * cx + cy * cy));
     const float lg = a.lam_in[(size_t)(kQ + i) * a.nv + v];
-    a.mu[(size_t)(kQ + i) * a.nv + v] = has_g ? (1.f - om) * lg + om * z3 : 0.f;
+    a.mu[(size_t)i * a.nv + v] =
+        make_float2((1.f - om) * lf + om * (z0 + z1 * cx + z2 * cy + z3 * (cx * cx + cy * cy)),
+                    has_g ? (1.f - om) * lg + om * z3 : 0.f);
   }
 }
 
-__global__ void __launch_bounds__(128) adjoint_stream_kernel(const __grid_constant__ AdjointArgs a) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)kQ * a.nv) return;
-  const int i = (int)(t / a.nv);
-  const long long u = t % a.nv;
-  const int ia = i / 5, ib = i % 5;
-  float accf = 0.f, accg = 0.f;
-  const float* mf = a.mu + (size_t)i * a.nv;
-  const float* mg = a.mu + (size_t)(kQ + i) * a.nv;
-  if (a.mapped) {
-    const long long* ptr = a.tm_ptr + (size_t)i * (a.nv + 1);
-    for (long long e = ptr[u]; e < ptr[u + 1]; ++e) {
-      const int src = a.tm_col[e];
-      accf += a.tm_w[e] * mf[src];
-      accg += a.tm_w[e] * mg[src];
-    }
-  } else {
-    const int x = (int)(u % a.nx), y = (int)(u / a.nx);
-    const int* px = a.tx_ptr + ia * (a.nx + 1);
-    const int* py = a.ty_ptr + ib * (a.ny + 1);
-    for (int ey = py[y]; ey < py[y + 1]; ++ey) {
-      const float wy = a.ty_w[ey];
-      const size_t row = (size_t)a.ty_col[ey] * a.nx;
-      float sf = 0.f, sg = 0.f;
-      for (int ex = px[x]; ex < px[x + 1]; ++ex) {
-        sf += a.tx_w[ex] * mf[row + a.tx_col[ex]];
-        sg += a.tx_w[ex] * mg[row + a.tx_col[ex]];
-      }
-      accf += wy * sf;
-      accg += wy * sg;
-    }
+// S^T on a uniform grid, separable like S: first along x (thread = plane, row, target column:
+// the entries of the column's transposed x stencil), then along y into lambda (thread = plane,
+// target row, column).  Each pass reads its entries from one row / one column of the plane.
+// Grid of the streaming kernels: x = blockIdx.x * 256 + threadIdx.x, plane i = blockIdx.z, rows
+// y = blockIdx.y, + gridDim.y, ... (no integer division per thread).
+template <int KW>
+__global__ void __launch_bounds__(256) adjoint_stream_x_kernel(const __grid_constant__ AdjointArgs a) {
+  const int x = blockIdx.x * 256 + threadIdx.x, i = blockIdx.z, ia = i / 5;
+  if (x >= a.nx) return;
+  // the column's transposed x stencil, once for all the rows this thread does
+  const size_t e0 = ((size_t)ia * a.nx + x) * a.kw;
+  const int deg = __ldg(a.tx_deg + (size_t)ia * a.nx + x);
+  int col[KW];
+  float w[KW];
+#pragma unroll
+  for (int k = 0; k < KW; ++k) {
+    col[k] = k < deg ? __ldg(a.tx_col + e0 + k) : x;
+    w[k] = k < deg ? __ldg(a.tx_w + e0 + k) : 0.f;
   }
-  a.lam_out[(size_t)i * a.nv + u] = accf;
-  a.lam_out[(size_t)(kQ + i) * a.nv + u] = (a.cp.npop == 2) ? accg : 0.f;
+  for (int y = blockIdx.y; y < a.ny; y += gridDim.y) {
+    const size_t row = (size_t)i * a.nv + (size_t)y * a.nx;
+    const float2* mrow = a.mu + row;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < KW; ++k)
+      if (k < deg) acc = fma2(bcast2(w[k]), __ldg(mrow + col[k]), acc);
+    a.tmp[row + x] = acc;
+  }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(256) adjoint_stream_y_kernel(const __grid_constant__ AdjointArgs a) {
+  const int x = blockIdx.x * 256 + threadIdx.x, i = blockIdx.z, ib = i % 5;
+  if (x >= a.nx) return;
+  const float2* colp = a.tmp + (size_t)i * a.nv + x;
+  for (int y = blockIdx.y; y < a.ny; y += gridDim.y) {
+    // the row's transposed y stencil: KW entries in 16-byte rows (the same for the whole block)
+    const size_t e0 = ((size_t)ib * a.ny + y) * KW;
+    const int deg = __ldg(a.ty_deg + (size_t)ib * a.ny + y);
+    int row[KW];
+    float w[KW];
+#pragma unroll
+    for (int k = 0; k < KW; k += 4) {
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(a.ty_col + e0 + k));
+      const float4 w4 = __ldg(reinterpret_cast<const float4*>(a.ty_w + e0 + k));
+      row[k] = c4.x; row[k + 1] = c4.y; row[k + 2] = c4.z; row[k + 3] = c4.w;
+      w[k] = w4.x; w[k + 1] = w4.y; w[k + 2] = w4.z; w[k + 3] = w4.w;
+    }
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < KW; ++k)
+      if (k < deg) acc = fma2(bcast2(w[k]), __ldg(colp + (size_t)row[k] * a.nx), acc);
+    const size_t u = (size_t)y * a.nx + x;
+    a.lam_out[(size_t)i * a.nv + u] = acc.x;
+    a.lam_out[(size_t)(kQ + i) * a.nv + u] = (a.cp.npop == 2) ? acc.y : 0.f;
+  }
+}
+
+// S^T on a mapped grid: CSR over the target vertex, per velocity.
+__global__ void __launch_bounds__(256) adjoint_stream_mapped_kernel(const __grid_constant__ AdjointArgs a) {
+  const int x = blockIdx.x * 256 + threadIdx.x, i = blockIdx.z;
+  if (x >= a.nx) return;
+  const float2* m = a.mu + (size_t)i * a.nv;
+  const long long* ptr = a.tm_ptr + (size_t)i * (a.nv + 1);
+  for (int y = blockIdx.y; y < a.ny; y += gridDim.y) {
+    const long long u = (long long)y * a.nx + x;
+    float2 acc = make_float2(0.f, 0.f);
+    for (long long e = ptr[u]; e < ptr[u + 1]; ++e) acc = fma2(bcast2(a.tm_w[e]), __ldg(m + a.tm_col[e]), acc);
+    a.lam_out[(size_t)i * a.nv + u] = acc.x;
+    a.lam_out[(size_t)(kQ + i) * a.nv + u] = (a.cp.npop == 2) ? acc.y : 0.f;
+  }
 }
 
 cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
-  const int threads = 128;
-  adjoint_collide_kernel<<<(unsigned)((a.nv + threads - 1) / threads), threads, 0, s>>>(a);
+  adjoint_collide_kernel<<<(unsigned)((a.nv + 127) / 128), 128, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const long long n = (long long)kQ * a.nv;
-  adjoint_stream_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(a);
+  const dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)(a.ny < 65535 ? a.ny : 65535), kQ);
+  if (a.mapped) {
+    adjoint_stream_mapped_kernel<<<grid, 256, 0, s>>>(a);
+  } else {
+    const dim3 gx(grid.x, (unsigned)((a.ny + 15) / 16 < 65535 ? (a.ny + 15) / 16 : 65535), kQ);
+    switch (a.kw) {   // x: 16 rows per thread, the column's stencil loaded once
+      case 4: adjoint_stream_x_kernel<4><<<gx, 256, 0, s>>>(a); adjoint_stream_y_kernel<4><<<grid, 256, 0, s>>>(a); break;
+      case 8: adjoint_stream_x_kernel<8><<<gx, 256, 0, s>>>(a); adjoint_stream_y_kernel<8><<<grid, 256, 0, s>>>(a); break;
+      case 12: adjoint_stream_x_kernel<12><<<gx, 256, 0, s>>>(a); adjoint_stream_y_kernel<12><<<grid, 256, 0, s>>>(a); break;
+      case 16: adjoint_stream_x_kernel<16><<<gx, 256, 0, s>>>(a); adjoint_stream_y_kernel<16><<<grid, 256, 0, s>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -70,7 +70,9 @@ struct sllbm_ctx {
   // adjoint
   bool transposed = false;
   float* mu = nullptr;
-  int *tx_ptr = nullptr, *tx_col = nullptr, *ty_ptr = nullptr, *ty_col = nullptr;
+  int *tx_col = nullptr, *ty_col = nullptr, tkw = 0;   // fixed-width transposed stencils
+  int *tx_deg = nullptr, *ty_deg = nullptr;
+  float2* atmp = nullptr;                               // between the x and y passes of S^T
   float *tx_w = nullptr, *ty_w = nullptr;
   long long* tm_ptr = nullptr;
   int* tm_col = nullptr;
@@ -911,47 +913,51 @@ sllbm_status sllbm_moments(sllbm_ctx* c, float* rho, float* u, float* v, float* 
 }
 
 // ---- transposed stencils for the adjoint (host build from the FP64 tables) ----
-static sllbm_status build_axis_transpose(sllbm_ctx* c, const AxisK& ax, const int* off_dev,
-                                         const double* w_dev, int** ptr_dev, int** col_dev, float** w_out) {
+// Per axis, component and node j: the (vertex, weight) pairs of the vertices whose stencil reads
+// j, in ascending vertex order (deterministic).
+struct AxisTranspose {
+  std::vector<std::vector<std::pair<int, float>>> rows;   // [comp * n + j]
+  size_t max_deg = 0;
+};
+
+static sllbm_status axis_transpose(sllbm_ctx* c, const AxisK& ax, const int* off_dev, const double* w_dev,
+                                   AxisTranspose* t) {
   const int n = ax.nv, P = c->P;
   std::vector<int> off((size_t)kQ1 * n);
   std::vector<double> w((size_t)kQ1 * n * (P + 1));
   CUDA_TRY(c, cudaMemcpyAsync(off.data(), off_dev, off.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(w.data(), w_dev, w.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  std::vector<int> ptr((size_t)kQ1 * (n + 1), 0);
-  // count entries per (component, source vertex)
+  t->rows.assign((size_t)kQ1 * n, {});
   for (int comp = 0; comp < kQ1; ++comp)
     for (int j = 0; j < n; ++j)
       for (int k = 0; k <= P; ++k) {
         const int src = wrap_index(j + off[(size_t)comp * n + j] + k, n, ax.periodic);
-        ptr[(size_t)comp * (n + 1) + src + 1]++;
+        t->rows[(size_t)comp * n + src].push_back({j, (float)w[((size_t)comp * n + j) * (P + 1) + k]});
       }
-  std::vector<int> start(ptr.size());
-  size_t total = 0;
-  for (int comp = 0; comp < kQ1; ++comp) {
-    int* p0 = &ptr[(size_t)comp * (n + 1)];
-    p0[0] = (int)total;
-    for (int j = 0; j < n; ++j) p0[j + 1] += p0[j];
-    total = p0[n];
+  for (const auto& r : t->rows) t->max_deg = std::max(t->max_deg, r.size());
+  return SLLBM_OK;
+}
+
+// Fixed-width copy of a transpose: kw entries per (comp, node), padded with weight 0 on the node.
+static sllbm_status upload_transpose(sllbm_ctx* c, const AxisTranspose& t, int n, int kw, int** col_dev,
+                                     float** w_dev, int** deg_dev) {
+  std::vector<int> col(t.rows.size() * kw), deg(t.rows.size());
+  std::vector<float> wt(t.rows.size() * kw, 0.f);
+  for (size_t r = 0; r < t.rows.size(); ++r) {
+    deg[r] = (int)t.rows[r].size();
+    for (int k = 0; k < kw; ++k) {
+      const bool have = (size_t)k < t.rows[r].size();
+      col[r * kw + k] = have ? t.rows[r][k].first : (int)(r % n);
+      wt[r * kw + k] = have ? t.rows[r][k].second : 0.f;
+    }
   }
-  std::vector<int> col(total);
-  std::vector<float> wt(total);
-  std::vector<int> fill(ptr.begin(), ptr.end());
-  for (int comp = 0; comp < kQ1; ++comp)
-    for (int j = 0; j < n; ++j)  // ascending target order within each row: deterministic
-      for (int k = 0; k <= P; ++k) {
-        const int src = wrap_index(j + off[(size_t)comp * n + j] + k, n, ax.periodic);
-        const int e = fill[(size_t)comp * (n + 1) + src]++;
-        col[e] = j;
-        wt[e] = (float)w[((size_t)comp * n + j) * (P + 1) + k];
-      }
-  TRY(dalloc(c, ptr_dev, ptr.size()));
-  TRY(dalloc(c, col_dev, total));
-  TRY(dalloc(c, w_out, total));
-  CUDA_TRY(c, cudaMemcpy(*ptr_dev, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CUDA_TRY(c, cudaMemcpy(*col_dev, col.data(), total * sizeof(int), cudaMemcpyHostToDevice));
-  CUDA_TRY(c, cudaMemcpy(*w_out, wt.data(), total * sizeof(float), cudaMemcpyHostToDevice));
+  TRY(dalloc(c, col_dev, col.size()));
+  TRY(dalloc(c, w_dev, wt.size()));
+  TRY(dalloc(c, deg_dev, deg.size()));
+  CUDA_TRY(c, cudaMemcpy(*col_dev, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(*w_dev, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(*deg_dev, deg.data(), deg.size() * sizeof(int), cudaMemcpyHostToDevice));
   return SLLBM_OK;
 }
 
@@ -1028,18 +1034,25 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
   const bool mapped = c->map.kind != SLLBM_MAP_IDENTITY;
   if (!c->transposed) {
     if (!c->mu) TRY(dalloc(c, &c->mu, (size_t)2 * kQ * c->nv));
-    if (mapped)
+    if (mapped) {
       TRY(build_mapped_transpose(c));
-    else {
-      TRY(build_axis_transpose(c, c->ax, c->offx, c->wx64, &c->tx_ptr, &c->tx_col, &c->tx_w));
-      TRY(build_axis_transpose(c, c->ay, c->offy, c->wy64, &c->ty_ptr, &c->ty_col, &c->ty_w));
+    } else {
+      AxisTranspose tx, ty;
+      TRY(axis_transpose(c, c->ax, c->offx, c->wx64, &tx));
+      TRY(axis_transpose(c, c->ay, c->offy, c->wy64, &ty));
+      const int kw = (int)((std::max(tx.max_deg, ty.max_deg) + 3) / 4 * 4);   // 16-byte rows
+      if (kw > 16) return fail(c, SLLBM_ERR_UNSUPPORTED, "adjoint: more than 16 stencils read one node");
+      TRY(upload_transpose(c, tx, c->nx, kw, &c->tx_col, &c->tx_w, &c->tx_deg));
+      TRY(upload_transpose(c, ty, c->ny, kw, &c->ty_col, &c->ty_w, &c->ty_deg));
+      TRY(dalloc(c, &c->atmp, (size_t)kQ * c->nv));
+      c->tkw = kw;
     }
     c->transposed = true;
   }
   AdjointArgs a{};
   a.lam_in = lam_in;
   a.lam_out = lam_out;
-  a.mu = c->mu;
+  a.mu = reinterpret_cast<float2*>(c->mu);
   a.moments = moments;
   a.nx = c->nx;
   a.ny = c->ny;
@@ -1047,12 +1060,14 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
   a.cs = c->cs;
   a.cp = c->cp;
   a.mapped = mapped;
-  a.tx_ptr = c->tx_ptr;
+  a.kw = c->tkw;
   a.tx_col = c->tx_col;
   a.tx_w = c->tx_w;
-  a.ty_ptr = c->ty_ptr;
+  a.tx_deg = c->tx_deg;
   a.ty_col = c->ty_col;
   a.ty_w = c->ty_w;
+  a.ty_deg = c->ty_deg;
+  a.tmp = c->atmp;
   a.tm_ptr = c->tm_ptr;
   a.tm_col = c->tm_col;
   a.tm_w = c->tm_w;

@@ -154,20 +154,23 @@ cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s);
 struct AdjointArgs {
   const float* lam_in;
   float* lam_out;
-  float* mu;           // [2][25][nv] scratch: J_C^T lambda
+  float2* mu;          // [25][nv] scratch: J_C^T lambda as (f, g) pairs
   const float* moments;  // [4][nv]
   int nx, ny;
   long long nv;
   Consts cs;
   CollideK cp;
-  // transposed stencils: uniform per axis (CSR over vertex index per component), mapped per velocity
+  // transposed stencils: uniform per axis (fixed width kw per (component, node), padded with
+  // zero weights), mapped per velocity (CSR over vertex index)
   int mapped;
-  const int* tx_ptr;   // [5][nx+1]
-  const int* tx_col;
+  int kw;
+  const int* tx_col;   // [5][nx][kw]
   const float* tx_w;
-  const int* ty_ptr;   // [5][ny+1]
-  const int* ty_col;
+  const int* tx_deg;   // [5][nx]: entries in use
+  const int* ty_col;   // [5][ny][kw]
   const float* ty_w;
+  const int* ty_deg;   // [5][ny]
+  float2* tmp;         // [25][nv] scratch between the x and y passes of the uniform S^T
   const long long* tm_ptr;  // [25][nv+1]
   const int* tm_col;
   const float* tm_w;
