@@ -329,6 +329,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": clocks,
             "e2e": e2e,
+            "f_only_value": value / 2,   # the same time counted in f updates only
             "adjoint": adjoint,
             "gpu_launches": args.steps * s.launches_per_step,
             "mass_after": m["mass"],
