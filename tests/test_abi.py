@@ -39,3 +39,35 @@ def test_status_strings_without_gpu():
     p.tau = 0.4
     assert lib.sllbm_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h)) == sllbm.ERR_ARG
     assert lib.sllbm_create(None, ctypes.byref(p), None, ctypes.byref(h)) == sllbm.ERR_ARG
+
+
+def test_host_validation_of_sizes_and_options():
+    """Size limits and option combinations are rejected on the host, before any CUDA call."""
+    lib = sllbm.load()
+    h = ctypes.c_void_p()
+
+    def create(g, p):
+        return lib.sllbm_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h))
+
+    ok_grid = lambda: sllbm.GridDesc(4, 4, 2, 0.0, 1.0, 0.0, 1.0, 0, 0, 0, 0, (ctypes.c_double * 4)())
+    ok_params = lambda: sllbm.Params(0, 0.01, 0.8, 2.5, 1.0, 0, 1.0, 0)
+    g = ok_grid()
+    g.nx_cells = (1 << 20) // 2 + 1          # more than 2^20 vertices on an axis
+    assert create(g, ok_params()) == sllbm.ERR_UNSUPPORTED
+    g = ok_grid()
+    g.nx_cells = 0                           # empty grid
+    assert create(g, ok_params()) == sllbm.ERR_ARG
+    g = ok_grid()
+    g.x1 = g.x0                              # degenerate domain
+    assert create(g, ok_params()) == sllbm.ERR_ARG
+    g = ok_grid()
+    g.bc_x = 7
+    assert create(g, ok_params()) == sllbm.ERR_ARG
+    for field, value, status in (("pr", -1.0, sllbm.ERR_ARG), ("pr", float("nan"), sllbm.ERR_ARG),
+                                 ("isothermal", 1, sllbm.ERR_ARG),      # needs cv = 1
+                                 ("isothermal", 2, sllbm.ERR_ARG), ("T0", 2.0, sllbm.ERR_ARG),
+                                 ("dt", 0.0, sllbm.ERR_ARG), ("cv", 0.5, sllbm.ERR_ARG),
+                                 ("velset", 1, sllbm.ERR_UNSUPPORTED), ("prec", 9, sllbm.ERR_ARG)):
+        p = ok_params()
+        setattr(p, field, value)
+        assert create(ok_grid(), p) == status, (field, value)

@@ -1,7 +1,7 @@
 """Every interpolation order p = 1..4, both node families, both storage types and both grid
 kinds against the oracle (FP32 <= 1e-5 after one step, <= 1e-4 after 30 steps; FP64 populations
-element by element), including a grid whose tiles are ragged in both directions and a
-zero-gradient axis on each side of the domain.
+element by element), including a grid whose tiles are ragged in both directions, zero-gradient
+axes, and degenerate grids of one or two cells (which run in the gather kernel).
 """
 import dataclasses
 
@@ -27,6 +27,9 @@ CASES = {
     "p2_equidistant": _tgv(2, 17, 11, nodes="equidistant"),
     "p3": _tgv(3, 12, 9),
     "p4_clamped": _tgv(4, 11, 6, bc=(W.ZERO_GRADIENT, W.ZERO_GRADIENT)),
+    "tiny_p2_one_cell": _tgv(2, 1, 1),
+    "tiny_p4_clamped": _tgv(4, 2, 3, bc=(W.ZERO_GRADIENT, W.ZERO_GRADIENT)),
+    "tiny_p3_mixed": _tgv(3, 1, 2, bc=(W.PERIODIC, W.ZERO_GRADIENT)),
     "p3_mapped": dataclasses.replace(W.svi(), order=3).resized(14, 8, steps=30, dt=0.01),
     "p4_mapped": dataclasses.replace(W.svi(), order=4).resized(10, 6, steps=30, dt=0.01),
 }
