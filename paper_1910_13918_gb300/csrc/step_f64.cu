@@ -5,7 +5,7 @@
 
 namespace sllbm {
 
-template <int P, bool Mapped>
+template <int P, bool Mapped, bool PR>
 __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_constant__ StepArgs a) {
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= a.nv) return;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_consta
   const size_t o = (size_t)iy * a.pitch + (size_t)ix * a.xs;
   // Pr != 1 (Sec. II.C): non-equilibrium centred third moments of f and g (xxx, xxy, xyy, yyy)
   double qf[4] = {0.0, 0.0, 0.0, 0.0}, qg[4] = {0.0, 0.0, 0.0, 0.0};
-  if (a.cp.pr_on) {
+  if (PR) {
 #pragma unroll 1
     for (int i = 0; i < kQ; ++i) {
       const int ia = i / 5, ib = i % 5;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_consta
       const double feq = a.cs.w[ia] * a.cs.w[ib] * rho * (1.0 + eq_em1<double>(e, ia, ib));
       // quasi-equilibrium: w_a w_b (Q_xxx h3(a) + Q_xxy h2(a) h1(b) + Q_xyy h1(a) h2(b) + Q_yyy h3(b))
       double sf = 0.0, sg = 0.0;
-      if (a.cp.pr_on) {
+      if (PR) {
         const double wab = a.cs.w[ia] * a.cs.w[ib];
         const double h[4] = {a.cs.he[3][ia], a.cs.he[2][ia] * a.cs.he[1][ib],
                              a.cs.he[1][ia] * a.cs.he[2][ib], a.cs.he[3][ib]};
@@ -119,9 +119,11 @@ static cudaError_t launch_p(const StepArgs& a, cudaStream_t s) {
   const int threads = 128;
   const unsigned blocks = (unsigned)((a.nv + threads - 1) / threads);
   if (a.mapped)
-    step_plain_f64_kernel<P, true><<<blocks, threads, 0, s>>>(a);
+    a.cp.pr_on ? step_plain_f64_kernel<P, true, true><<<blocks, threads, 0, s>>>(a)
+               : step_plain_f64_kernel<P, true, false><<<blocks, threads, 0, s>>>(a);
   else
-    step_plain_f64_kernel<P, false><<<blocks, threads, 0, s>>>(a);
+    a.cp.pr_on ? step_plain_f64_kernel<P, false, true><<<blocks, threads, 0, s>>>(a)
+               : step_plain_f64_kernel<P, false, false><<<blocks, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
