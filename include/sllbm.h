@@ -6,8 +6,10 @@
  * Table I), fourth-order equilibrium (Sec. II.A, Eqs. moments), a second population g for the
  * heat-capacity ratio (Sec. II.D), cell-wise Lagrange interpolation of order p <= 4 on
  * Gauss-Lobatto-Chebyshev support points (Sec. II.E, Eq. sl_streaming), and the lattice
- * Boltzmann equations of Eq. streaming_fg with Prandtl number 1.  It also provides the adjoint of
- * one step, which the paper does not have.
+ * Boltzmann equations of Eq. streaming_fg (Prandtl number 1, or another through the
+ * quasi-equilibrium term of Sec. II.C), with the isothermal configuration of Sec. III.A as an
+ * option.  It also provides the adjoint of one step (Prandtl number 1), which the paper does not
+ * have.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
