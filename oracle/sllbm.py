@@ -10,6 +10,8 @@ Arrays
 ------
 A population field is ``F[i, iy, ix]`` with ``i = 5*a + b`` the D2Q25 index (``a`` the D1Q5 index
 of the x component, ``b`` of the y component), ``iy`` the vertex row and ``ix`` the vertex column.
+The D2Q9 set of the comparison in Sec. III.A is carried the same way (``i = 3*a + b``, D1Q3
+indices); a field's velocity set is told by its first axis (25 or 9).
 The state of the method is the pair ``(f, g)`` of *post-collision* vertex values (full
 populations, not deviations).
 
@@ -33,7 +35,8 @@ import math
 import numpy as np
 
 D = 2          # spatial dimension
-Q = 25         # D2Q25
+Q = 25         # D2Q25 (the default velocity set)
+Q9 = 9         # D2Q9, the standard set the paper compares against (Sec. III.A)
 T0 = 1.0       # reference temperature; c_s^2 = R*T0 = 1 with R = 1 (Sec. II.A, II.B)
 
 
@@ -67,6 +70,36 @@ def d2q25():
             xi[i, 1] = x1[b]
             w[i] = w1[a] * w1[b]
     return xi, w
+
+
+def d1q3():
+    """D1Q3 abscissae and weights (the standard three-point Gauss-Hermite rule, c_s = 1):
+    index 0: 0; indices 1, 2: +sqrt(3), -sqrt(3).  Weights 2/3, 1/6, 1/6."""
+    s3 = math.sqrt(3.0)
+    return np.array([0.0, s3, -s3]), np.array([2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0])
+
+
+def d2q9():
+    """D2Q9 set as the tensor product of D1Q3: i = 3a + b, xi_i = (xi_a, xi_b), w_i = w_a w_b."""
+    x1, w1 = d1q3()
+    xi = np.zeros((Q9, D))
+    w = np.zeros(Q9)
+    for a in range(3):
+        for b in range(3):
+            i = 3 * a + b
+            xi[i, 0] = x1[a]
+            xi[i, 1] = x1[b]
+            w[i] = w1[a] * w1[b]
+    return xi, w
+
+
+def velocity_set(q=Q):
+    """(xi, w) of the set with q velocities: 25 (D2Q25, the method's set) or 9 (D2Q9)."""
+    if q == Q:
+        return d2q25()
+    if q == Q9:
+        return d2q9()
+    raise ValueError(f"no velocity set with {q} velocities")
 
 
 # ---------------------------------------------------------------------------------------------
@@ -128,16 +161,17 @@ def a_eq(n, idx, rho, u, theta):
     raise ValueError("equilibrium coefficients are given up to fourth order")
 
 
-def equilibrium_f(rho, u, theta):
-    """Discrete fourth-order equilibrium f_i^eq, shape (Q,) + vertex shape.
+def equilibrium_f(rho, u, theta, q=Q):
+    """Discrete fourth-order equilibrium f_i^eq, shape (q,) + vertex shape.
 
     f_i^eq = w_i sum_{n=0}^{4} (1/n!) a_eq^(n) : H^(n)(xi_i)    (Eq. equilibrium with Eq. discrete)
-    The full contraction runs over every index tuple in {x, y}^n.
+    The full contraction runs over every index tuple in {x, y}^n.  The same fourth-order
+    expansion serves the D2Q9 set (q = 9), as in the comparison of Sec. III.A.
     """
-    xi, w = d2q25()
+    xi, w = velocity_set(q)
     rho = np.asarray(rho)
-    out = np.zeros((Q,) + rho.shape, dtype=np.result_type(rho, u, theta, np.float64))
-    for i in range(Q):
+    out = np.zeros((q,) + rho.shape, dtype=np.result_type(rho, u, theta, np.float64))
+    for i in range(q):
         acc = np.zeros(rho.shape, dtype=out.dtype)
         for n in range(5):
             # H^(n) at one velocity is a scalar per index tuple; a_eq carries the vertex shape
@@ -149,9 +183,9 @@ def equilibrium_f(rho, u, theta):
     return out
 
 
-def equilibrium_g(rho, u, theta, cv):
+def equilibrium_g(rho, u, theta, cv, q=Q):
     """Second population equilibrium g_i^eq = (2 C_v - D) theta f_i^eq (Sec. II.D)."""
-    return (2.0 * cv - D) * theta * equilibrium_f(rho, u, theta)
+    return (2.0 * cv - D) * theta * equilibrium_f(rho, u, theta, q)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -164,11 +198,11 @@ def macroscopic(f, g, cv):
     T = (2 rho E - rho |u|^2) / (2 C_v rho)  (gas constant R = 1, T0 = 1).
     Returns (rho, u, theta) with u carrying a trailing D axis.
     """
-    xi, _ = d2q25()
+    xi, _ = velocity_set(f.shape[0])
     rho = np.zeros(f.shape[1:], dtype=f.dtype)
     j = np.zeros(f.shape[1:] + (D,), dtype=f.dtype)
     e2 = np.zeros(f.shape[1:], dtype=f.dtype)
-    for i in range(Q):
+    for i in range(f.shape[0]):
         rho = rho + f[i]
         j[..., 0] = j[..., 0] + f[i] * xi[i, 0]
         j[..., 1] = j[..., 1] + f[i] * xi[i, 1]
@@ -180,9 +214,9 @@ def macroscopic(f, g, cv):
 
 def total_energy_density(f, g):
     """rho E = (sum f |xi|^2 + sum g) / 2 per vertex (Eq. E)."""
-    xi, _ = d2q25()
+    xi, _ = velocity_set(f.shape[0])
     e2 = np.zeros(f.shape[1:], dtype=f.dtype)
-    for i in range(Q):
+    for i in range(f.shape[0]):
         e2 = e2 + f[i] * (xi[i, 0] ** 2 + xi[i, 1] ** 2) + g[i]
     return 0.5 * e2
 
@@ -194,23 +228,23 @@ def centered_third_moment(F, u):
     """Centred third moment Q[a, b, c] = sum_i F_i (xi_i - u)_a (xi_i - u)_b (xi_i - u)_c of a
     population field (the centred heat-flux tensor of Sec. II.C), shape (D, D, D) + vertex shape.
     ``u`` has the vertex shape plus a trailing D axis."""
-    xi, _ = d2q25()
+    xi, _ = velocity_set(F.shape[0])
     out = np.zeros((D, D, D) + F.shape[1:], dtype=F.dtype)
-    for i in range(Q):
+    for i in range(F.shape[0]):
         c = [xi[i, k] - u[..., k] for k in range(D)]
         for a, b, cc in itertools.product(range(D), repeat=3):
             out[a, b, cc] = out[a, b, cc] + F[i] * c[a] * c[b] * c[cc]
     return out
 
 
-def quasi_equilibrium(Qneq):
+def quasi_equilibrium(Qneq, q=Q):
     """f*_i = w_i Q^neq : H^(3)(xi_i) / 3! (Sec. II.C): the full contraction over the D^3 index
     tuples of the non-equilibrium centred third moment with the third Hermite tensor, weighted by
     the lattice weight.  The 1/3! is the Hermite normalisation of the third-order term (the
     printed formula has no prefactor); with it the third moment of f* is Q^neq."""
-    xi, w = d2q25()
-    out = np.zeros((Q,) + Qneq.shape[3:], dtype=Qneq.dtype)
-    for i in range(Q):
+    xi, w = velocity_set(q)
+    out = np.zeros((q,) + Qneq.shape[3:], dtype=Qneq.dtype)
+    for i in range(q):
         acc = np.zeros(Qneq.shape[3:], dtype=Qneq.dtype)
         for idx in itertools.product(range(D), repeat=3):
             acc = acc + Qneq[idx] * hermite(3, idx, xi[i])
@@ -229,26 +263,28 @@ def collide(f, g, tau, cv, pr=1.0, isothermal=False):
     f^eq, where f^qe (g^qe) is the quasi-equilibrium of the non-equilibrium centred third moment
     of f (of g).  With Pr = 1, tau_Pr = tau and the quasi-equilibrium term is zero: plain BGK.
     ``isothermal``: the equilibrium at theta = 1 (the isothermal configuration of Sec. III.A).
+    The velocity set is that of the fields (25 or 9 velocities).
     """
+    q = f.shape[0]
     rho, u, theta = macroscopic(f, g, cv)
     if isothermal:
         theta = np.ones_like(theta)
-    feq = equilibrium_f(rho, u, theta)
+    feq = equilibrium_f(rho, u, theta, q)
     geq = (2.0 * cv - D) * theta * feq
     fn, gn = f - (f - feq) / tau, g - (g - geq) / tau
     if pr != 1.0:
         c = 1.0 / tau - 1.0 / tau_prandtl(tau, pr)
-        fn = fn + c * quasi_equilibrium(centered_third_moment(f, u) - centered_third_moment(feq, u))
-        gn = gn + c * quasi_equilibrium(centered_third_moment(g, u) - centered_third_moment(geq, u))
+        fn = fn + c * quasi_equilibrium(centered_third_moment(f, u) - centered_third_moment(feq, u), q)
+        gn = gn + c * quasi_equilibrium(centered_third_moment(g, u) - centered_third_moment(geq, u), q)
     return fn, gn
 
 
-def initial_state(rho, u, v, T, cv):
+def initial_state(rho, u, v, T, cv, q=Q):
     """Post-collision state at t = 0: the equilibrium of the given fields (collision keeps it)."""
     uu = np.stack([np.asarray(u, dtype=np.result_type(u, np.float64)),
                    np.asarray(v, dtype=np.result_type(v, np.float64))], axis=-1)
     theta = np.asarray(T) / T0
-    feq = equilibrium_f(np.asarray(rho), uu, theta)
+    feq = equilibrium_f(np.asarray(rho), uu, theta, q)
     return feq, (2.0 * cv - D) * theta * feq
 
 
@@ -415,13 +451,14 @@ class Departures:
     x_d = x_v - dt xi_i (Eq. streaming_fg), folded into the domain per axis, then located in a
     cell.  On a transformed grid the fold is done on the physical point and the reference point
     is found by Newton inversion of the map.  ``vertices`` optionally restricts the computation
-    to a flat list of vertex indices (row-major, iy * nx + ix).
+    to a flat list of vertex indices (row-major, iy * nx + ix).  ``q`` picks the velocity set.
     """
 
-    def __init__(self, grid: Grid, dt: float, vertices=None):
+    def __init__(self, grid: Grid, dt: float, vertices=None, q=Q):
         self.grid = grid
         self.dt = float(dt)
-        xi, _ = d2q25()
+        self.q = q
+        xi, _ = velocity_set(q)
         X, Y = grid.coords()
         RX, RY = grid.reference_coords()
         X, Y, RX, RY = (A.reshape(-1) for A in (X, Y, RX, RY))
@@ -431,7 +468,7 @@ class Departures:
         self.vertices = vertices
         ax, ay = grid.ax, grid.ay
         self.cx, self.cy, self.rx, self.ry = [], [], [], []
-        for i in range(Q):
+        for i in range(q):
             if grid.mapping is None:
                 xd = ax.fold(X - self.dt * xi[i, 0])
                 yd = ay.fold(Y - self.dt * xi[i, 1])
@@ -453,15 +490,16 @@ class Departures:
 def stream(F, dep: Departures):
     """Pull streaming (Eq. sl_streaming): F_pre[i](v) = sum_{a,b} psi_a(r) psi_b(s) F[i](node(a,b)).
 
-    ``F`` is the post-collision field of the previous step, shape (Q, ny, nx).  Returns the values
-    at the departure points for every vertex (shape (Q, ny, nx)), or for the vertex subset of
-    ``dep`` (shape (Q, len(subset))).
+    ``F`` is the post-collision field of the previous step, shape (q, ny, nx).  Returns the values
+    at the departure points for every vertex (shape (q, ny, nx)), or for the vertex subset of
+    ``dep`` (shape (q, len(subset))).
     """
     grid = dep.grid
     ax, ay, p = grid.ax, grid.ay, grid.p
+    assert F.shape[0] == dep.q, "field and departures belong to different velocity sets"
     shape = (grid.ny, grid.nx) if dep.vertices is None else (len(dep.vertices),)
-    out = np.zeros((Q,) + shape, dtype=F.dtype)
-    for i in range(Q):
+    out = np.zeros((dep.q,) + shape, dtype=F.dtype)
+    for i in range(dep.q):
         wx = lagrange(ax.nodes, dep.rx[i])
         wy = lagrange(ay.nodes, dep.ry[i])
         acc = np.zeros(dep.rx[i].shape, dtype=F.dtype)
