@@ -127,8 +127,9 @@ def _workload(name):
 
 
 def _workload_desc(w):
+    pops = "f and g populations" if w.n_populations == 2 else "f only (isothermal)"
     return (f"{w.name}: {w.nx}x{w.ny} vertices ({w.nx_cells}x{w.ny_cells} cells, p={w.order}), "
-            f"D2Q25, f and g populations, dt={w.dt:.6g}, tau={w.tau:.6g}")
+            f"{w.velset.upper()}, {pops}, dt={w.dt:.6g}, tau={w.tau:.6g}")
 
 
 # -------------------------------------------------------------------------------------------------
@@ -148,21 +149,22 @@ class OracleSample:
         self.grid = grid = o.Grid(ax, ay, o.SineMap(w.map_a) if w.map_a else None)
         X, Y = grid.coords()
         self.verts = np.arange(min(rows, grid.ny) * grid.nx)
-        dep0 = o.Departures(grid, w.dt, self.verts)
+        self.q = q = w.n_velocities
+        dep0 = o.Departures(grid, w.dt, self.verts, q=q)
         keys = []
-        for i in range(25):
+        for i in range(q):
             for b in range(grid.p + 1):
                 for a in range(grid.p + 1):
                     keys.append(ay.vertex_of(dep0.cy[i], b) * grid.nx + ax.vertex_of(dep0.cx[i], a))
         keys = np.unique(np.concatenate(keys))
         fields = [np.asarray(F).reshape(-1)[keys] for F in w.fields(X, Y)]
-        f0, g0 = o.initial_state(*fields, w.cv)
-        self.F = np.zeros((25, grid.ny * grid.nx))
-        self.G = np.zeros((25, grid.ny * grid.nx))
+        f0, g0 = o.initial_state(*fields, w.cv, q)
+        self.F = np.zeros((q, grid.ny * grid.nx))
+        self.G = np.zeros((q, grid.ny * grid.nx))
         self.F[:, keys] = f0
         self.G[:, keys] = g0
-        self.F = self.F.reshape(25, grid.ny, grid.nx)
-        self.G = self.G.reshape(25, grid.ny, grid.nx)
+        self.F = self.F.reshape(q, grid.ny, grid.nx)
+        self.G = self.G.reshape(q, grid.ny, grid.nx)
 
     @property
     def n_vertices(self):
@@ -171,10 +173,10 @@ class OracleSample:
     def step_time(self):
         o, w = self.o, self.w
         t = time.perf_counter()
-        dep = o.Departures(self.grid, w.dt, self.verts)
+        dep = o.Departures(self.grid, w.dt, self.verts, q=self.q)
         fpre = o.stream(self.F, dep)
         gpre = o.stream(self.G, dep)
-        o.collide(fpre, gpre, w.tau, w.cv)
+        o.collide(fpre, gpre, w.tau, w.cv, w.pr, w.isothermal)
         return time.perf_counter() - t
 
 
@@ -182,7 +184,8 @@ def cpu_baseline(w, rows=16, repeats=3):
     sample = OracleSample(w, rows)
     el = min(sample.step_time() for _ in range(repeats))
     nv = sample.n_vertices
-    return {"value": nv * 50 / el / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": nv * w.n_velocities * w.n_populations / el / 1e9, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
             "sample": f"one oracle step on the first {rows} vertex rows ({nv} vertices) of "
                       f"{w.name}, best of {repeats}: {el:.2f} s, numpy float64, one thread"}
 
@@ -198,7 +201,7 @@ def run_reference(args):
     times = [sample.step_time() for _ in range(args.steps)]
     nv = sample.n_vertices
     tot = sum(times)
-    value = nv * 50 * len(times) / tot / 1e9
+    value = nv * w.n_velocities * w.n_populations * len(times) / tot / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -304,11 +307,16 @@ def run_ours(args):
 
     if rank == 0:
         peaks, src = _peaks()
-        bytes_per_update = {"f32": 8, "bf16": 4, "f64": 16}[args.prec]
+        # the stored state read once and written once: D2Q25 FP32/BF16 keeps (f, g) pairs (the g
+        # slot zero with one population), FP64 and D2Q9 keep the populations they have
+        stored = (w.n_velocities * w.n_populations
+                  if args.prec == "f64" or w.velset == "d2q9" else 2 * w.n_velocities)
+        elem = {"f32": 4, "bf16": 2, "f64": 8}[args.prec]
+        bytes_per_update = 2 * stored * elem / (w.n_velocities * w.n_populations)
         if s.kernel_name == "mapped_fused":
             # + the departure record of each (velocity, vertex): stencil origin and (r, s), 12 B,
-            # shared by f and g: 6 B per update
-            bytes_per_update += 6
+            # shared by the populations (6 B per update with f and g)
+            bytes_per_update += 12 / w.n_populations
         alg_bytes = updates * bytes_per_update
         achieved = alg_bytes / (ms_step * 1e-3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -329,7 +337,7 @@ def run_ours(args):
                          "algorithmic_bytes_per_launch": alg_bytes},
             "clocks": clocks,
             "e2e": e2e,
-            "f_only_value": value / 2,   # the same time counted in f updates only
+            "f_only_value": value / w.n_populations,   # the same time counted in f updates only
             "adjoint": adjoint,
             "gpu_launches": args.steps * s.launches_per_step,
             "mass_after": m["mass"],

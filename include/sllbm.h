@@ -8,8 +8,8 @@
  * Gauss-Lobatto-Chebyshev support points (Sec. II.E, Eq. sl_streaming), and the lattice
  * Boltzmann equations of Eq. streaming_fg (Prandtl number 1, or another through the
  * quasi-equilibrium term of Sec. II.C), with the isothermal configuration of Sec. III.A as an
- * option.  It also provides the adjoint of one step (Prandtl number 1), which the paper does not
- * have.
+ * option, and the standard D2Q9 set that Sec. III.A compares D2Q25 with (isothermal).  It also
+ * provides the adjoint of one step (D2Q25, Prandtl number 1), which the paper does not have.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -23,7 +23,8 @@
  * - Vertex arrays are row-major [ny][nx] (x fastest).  A population field is
  *   [n_pop][25][ny][nx] with velocity index i = 5a + b, a (b) the D1Q5 index of the x (y)
  *   component in the order of Table I: 0, +sqrt(5-sqrt10), +sqrt(5+sqrt10), -sqrt(5-sqrt10),
- *   -sqrt(5+sqrt10).  Population 0 is f, population 1 is g.
+ *   -sqrt(5+sqrt10).  Population 0 is f, population 1 is g.  With SLLBM_VEL_D2Q9 it is
+ *   [1][9][ny][nx], i = 3a + b with the D1Q3 components 0, +sqrt3, -sqrt3.
  * - The stored state is the post-collision population field (the field the next step
  *   interpolates).  With SLLBM_PREC_F32 / SLLBM_PREC_BF16_STORE it is stored as deviations
  *   f - w_i and g - (2 C_v - D) w_i; with SLLBM_PREC_F64_PLAIN as full populations in double.
@@ -59,7 +60,12 @@ typedef enum {
      * Sec. III.E); it needs the reference box [0, 2] x [0, 1] or any box it maps onto itself. */
     SLLBM_MAP_SINE = 1
 } sllbm_map;
-typedef enum { SLLBM_VEL_D2Q25_HERMITE = 0 } sllbm_velset;
+/* D2Q25: tensor product of the D1Q5 Gauss-Hermite rule (Sec. II.B, Table I), the method's set.
+ * D2Q9: tensor product of the three-point rule (0, +-sqrt3; weights 2/3, 1/6, 1/6), with the same
+ * fourth-order equilibrium (Sec. III.A); isothermal only (params.isothermal = 1, so cv = 1), plain
+ * BGK (pr 0 or 1), no adjoint and no equilibrium VJP (UNSUPPORTED otherwise).  Its state is one
+ * population in planar storage for every precision. */
+typedef enum { SLLBM_VEL_D2Q25_HERMITE = 0, SLLBM_VEL_D2Q9 = 1 } sllbm_velset;
 typedef enum {
     SLLBM_PREC_F32 = 0,         /* fused FP32 step, FP32 deviation storage                   */
     SLLBM_PREC_BF16_STORE = 1,  /* fused step with FP32 arithmetic and BF16 deviation storage */

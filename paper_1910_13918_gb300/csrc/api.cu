@@ -15,7 +15,7 @@
 
 using namespace sllbm;
 
-enum StepKernel { kKernelUniform = 0, kKernelGather = 1, kKernelPlainF64 = 2, kKernelMapped = 3 };
+enum StepKernel { kKernelUniform = 0, kKernelGather = 1, kKernelPlainF64 = 2, kKernelMapped = 3, kKernelQ9 = 4 };
 constexpr int kXferChunks = 5;   // host transfers move the state in this many plane groups
 
 struct sllbm_ctx {
@@ -23,10 +23,11 @@ struct sllbm_ctx {
   sllbm_params p;
   cudaStream_t stream = nullptr;
   int nx = 0, ny = 0, npop = 2, P = 0, store = kStoreF32, elem = 4;
+  int nq1 = kQ1, nq = kQ;                // velocity set: D2Q25, or D2Q9 (nq1 = 3, nq = 9)
   long long nv = 0;
   // State layout (StepArgs): value (pop, i, y, x) at i * plane_stride + pop * ps + y * pitch +
   // x * xs from the interior origin; pitchv vertices per row.  FP32/BF16: (f, g) interleaved
-  // (xs = 2, ps = 1); FP64: planar (xs = 1, ps = 25 planes).
+  // (xs = 2, ps = 1); FP64, and every D2Q9 state: planar (xs = 1, ps = nq planes).
   int pitchv = 0, pitch = 0, xs = 1;
   size_t plane_stride = 0;
   ptrdiff_t ps = 0;
@@ -119,15 +120,23 @@ static sllbm_status dalloc(sllbm_ctx* c, T** ptr, size_t count) {
     if (_s != SLLBM_OK) return _s;         \
   } while (0)
 
-// D1Q5 abscissae and weights in Table I order; he[k][a] = He_k(xi_a) / k! by the recurrence
-// He_{k+1}(x) = x He_k(x) - k He_{k-1}(x).
-static void build_consts(Consts& cs) {
+// D1Q5 abscissae and weights in Table I order (or the D1Q3 ones, 0, +sqrt3, -sqrt3 with
+// 2/3, 1/6, 1/6, for the D2Q9 set, the rest of the arrays zero); he[k][a] = He_k(xi_a) / k! by
+// the recurrence He_{k+1}(x) = x He_k(x) - k He_{k-1}(x).
+static void build_consts(Consts& cs, int velset) {
+  cs = Consts{};
   const double s10 = sqrt(10.0);
   const double sm = sqrt(5.0 - s10), lg = sqrt(5.0 + s10);
-  const double xi[5] = {0.0, sm, lg, -sm, -lg};
-  const double w[5] = {8.0 / 15.0, (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0,
-                       (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0};
-  for (int a = 0; a < 5; ++a) {
+  const double xi5[5] = {0.0, sm, lg, -sm, -lg};
+  const double w5[5] = {8.0 / 15.0, (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0,
+                        (7.0 + 2.0 * s10) / 60.0, (7.0 - 2.0 * s10) / 60.0};
+  const double xi3[5] = {0.0, sqrt(3.0), -sqrt(3.0), 0.0, 0.0};
+  const double w3[5] = {2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 0.0, 0.0};
+  const bool q9 = velset == SLLBM_VEL_D2Q9;
+  const double* xi = q9 ? xi3 : xi5;
+  const double* w = q9 ? w3 : w5;
+  cs.nq1 = q9 ? 3 : 5;
+  for (int a = 0; a < cs.nq1; ++a) {
     cs.xi[a] = xi[a];
     cs.w[a] = w[a];
     double hm1 = 0.0, h = 1.0, fact = 1.0;
@@ -476,14 +485,14 @@ static sllbm_status build_mapped_tiles(sllbm_ctx* c) {
 // context's copy stream) overlaps the conversion of the previous one (on its compute stream).
 static cudaError_t convert_state(sllbm_ctx* c, const void* src, void* dst, bool to_internal,
                                  int plane0, int nplanes) {
-  return launch_state_convert(src, dst, to_internal, c->elem, plane0, nplanes, c->nx, c->ny, c->pitch,
+  return launch_state_convert(src, dst, to_internal, c->elem, plane0, nplanes, c->nq, c->nx, c->ny, c->pitch,
                               c->plane_stride, c->xs, c->ps, c->stream);
 }
 
-static size_t dense_bytes(const sllbm_ctx* c) { return (size_t)c->npop * kQ * c->nv * c->elem; }
+static size_t dense_bytes(const sllbm_ctx* c) { return (size_t)c->npop * c->nq * c->nv * c->elem; }
 
 static sllbm_status copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
-  const int planes = c->npop * kQ;
+  const int planes = c->npop * c->nq;
   if (kind == cudaMemcpyDeviceToDevice) {
     CUDA_TRY(c, convert_state(c, src, dst, to_internal, 0, planes));
     return SLLBM_OK;
@@ -537,7 +546,7 @@ static cudaError_t fill_ghosts(sllbm_ctx* c) {
   if (c->xs == 2)
     return launch_ghost_fill(c->state[c->cur], 2 * c->elem, c->plane_stride / 2, c->pitchv, kQ,
                              c->ghost, c->stream);
-  return launch_ghost_fill(c->state[c->cur], c->elem, c->plane_stride, c->pitch, c->npop * kQ,
+  return launch_ghost_fill(c->state[c->cur], c->elem, c->plane_stride, c->pitch, c->npop * c->nq,
                            c->ghost, c->stream);
 }
 
@@ -579,7 +588,7 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   if (!g || !p || !out) return SLLBM_ERR_ARG;
   *out = nullptr;
   if (g->order < 1 || g->order > 4) return SLLBM_ERR_UNSUPPORTED;
-  if (p->velset != SLLBM_VEL_D2Q25_HERMITE) return SLLBM_ERR_UNSUPPORTED;
+  if (p->velset != SLLBM_VEL_D2Q25_HERMITE && p->velset != SLLBM_VEL_D2Q9) return SLLBM_ERR_UNSUPPORTED;
   if (g->nx_cells < 1 || g->ny_cells < 1 || !(g->x1 > g->x0) || !(g->y1 > g->y0)) return SLLBM_ERR_ARG;
   if ((g->bc_x != SLLBM_BC_PERIODIC && g->bc_x != SLLBM_BC_ZERO_GRADIENT) ||
       (g->bc_y != SLLBM_BC_PERIODIC && g->bc_y != SLLBM_BC_ZERO_GRADIENT))
@@ -591,6 +600,9 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   if (!(p->dt > 0.0) || !(p->tau > 0.5) || !(p->cv >= 1.0) || p->T0 != 1.0) return SLLBM_ERR_ARG;
   if (!(p->pr >= 0.0) || !(p->pr < 1e6)) return SLLBM_ERR_ARG;   // NaN, negative or absurd
   if (p->isothermal != 0 && (p->isothermal != 1 || p->cv != 1.0)) return SLLBM_ERR_ARG;
+  // D2Q9 carries the isothermal configuration only (Sec. III.A), with plain BGK
+  if (p->velset == SLLBM_VEL_D2Q9 && (p->isothermal != 1 || (p->pr != 0.0 && p->pr != 1.0)))
+    return SLLBM_ERR_UNSUPPORTED;
   if ((long long)g->nx_cells * g->order > (1 << 20) || (long long)g->ny_cells * g->order > (1 << 20))
     return SLLBM_ERR_UNSUPPORTED;
   sllbm_ctx* c = new (std::nothrow) sllbm_ctx();
@@ -599,7 +611,9 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   c->p = *p;
   c->stream = static_cast<cudaStream_t>(stream);
   c->P = g->order;
-  build_consts(c->cs);
+  build_consts(c->cs, p->velset);
+  c->nq1 = c->cs.nq1;
+  c->nq = c->nq1 * c->nq1;
   build_axis(c->ax, g->nx_cells, g->order, g->x0, g->x1, g->bc_x == SLLBM_BC_PERIODIC, g->nodes);
   build_axis(c->ay, g->ny_cells, g->order, g->y0, g->y1, g->bc_y == SLLBM_BC_PERIODIC, g->nodes);
   c->map.kind = g->map;
@@ -638,10 +652,10 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   c->gxr = (c->nx + 31) / 32 * 32 - c->nx + c->gx;
   c->rows_alloc = c->gy + c->ny + c->gyb;
   c->pitchv = (c->gx + c->nx + c->gxr + 7) / 8 * 8;
-  c->xs = (c->store == kStoreF64) ? 1 : 2;
+  c->xs = (c->store == kStoreF64 || c->nq1 == 3) ? 1 : 2;
   c->pitch = c->pitchv * c->xs;
   c->plane_stride = (size_t)c->rows_alloc * c->pitch;
-  c->ps = (c->xs == 2) ? 1 : (ptrdiff_t)kQ * c->plane_stride;
+  c->ps = (c->xs == 2) ? 1 : (ptrdiff_t)c->nq * c->plane_stride;
   c->ghost.on = 0;
   c->ghost.px = c->ax.periodic;
   c->ghost.py = c->ay.periodic;
@@ -652,7 +666,7 @@ sllbm_status sllbm_create(const sllbm_grid_desc* g, const sllbm_params* p, void*
   c->ghost.ylo = -c->gy;
   c->ghost.yhi = c->ny + c->gyb;
   sllbm_status s;
-  const size_t state_elems = (size_t)2 * kQ * c->rows_alloc * c->pitchv;
+  const size_t state_elems = (size_t)2 * c->nq * c->rows_alloc * c->pitchv;
   for (int k = 0; k < 2; ++k) {
     void* ptr = nullptr;
     s = dalloc(c, reinterpret_cast<char**>(&ptr), state_elems * c->elem);
@@ -694,7 +708,7 @@ sllbm_status sllbm_grid_info(const sllbm_ctx* c, int* nx, int* ny, int* npop) {
 
 sllbm_status sllbm_state_bytes(const sllbm_ctx* c, size_t* bytes) {
   if (!c || !bytes) return SLLBM_ERR_ARG;
-  *bytes = (size_t)c->npop * kQ * c->nv * c->elem;
+  *bytes = (size_t)c->npop * c->nq * c->nv * c->elem;
   return SLLBM_OK;
 }
 
@@ -726,7 +740,7 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
     }
     CUDA_TRY(c, launch_axis_tables(c->ax, c->cs, c->p.dt, c->offx, c->wx, c->wx64, c->stream));
     CUDA_TRY(c, launch_axis_tables(c->ay, c->cs, c->p.dt, c->offy, c->wy, c->wy64, c->stream));
-    std::vector<int> ox(kQ1 * (size_t)c->nx), oy(kQ1 * (size_t)c->ny);
+    std::vector<int> ox(c->nq1 * (size_t)c->nx), oy(c->nq1 * (size_t)c->ny);
     CUDA_TRY(c, cudaMemcpyAsync(ox.data(), c->offx, ox.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(oy.data(), c->offy, oy.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -736,7 +750,9 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
     c->offy_hi = *std::max_element(oy.begin(), oy.end()) + c->P;
   }
   c->n_fix = 0;
-  if (c->store == kStoreF64) {
+  if (c->nq1 == 3) {
+    c->kernel = kKernelQ9;
+  } else if (c->store == kStoreF64) {
     c->kernel = kKernelPlainF64;
   } else if (!mapped) {
     TRY(build_uniform_pattern(c));
@@ -757,7 +773,7 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
     }
     CUDA_TRY(c, launch_descriptors(g, c->dcx, c->dcy, c->dr, c->ds, c->dr64, c->ds64, c->stream));
   }
-  if (mapped && c->store != kStoreF64) {
+  if (mapped && c->store != kStoreF64 && c->kernel != kKernelQ9) {
     TRY(build_mapped_tiles(c));
     if (c->mt.valid) c->kernel = kKernelMapped;
   }
@@ -824,6 +840,7 @@ static cudaError_t enqueue_step(sllbm_ctx* c) {
       }
       break;
     case kKernelPlainF64: e = launch_step_plain_f64(a, c->stream); break;
+    case kKernelQ9: e = launch_step_q9(a, c->store, c->stream); break;
     default: e = launch_step_gather(a, c->store, c->stream); break;
   }
   if (e == cudaSuccess) c->cur ^= 1;
@@ -843,6 +860,7 @@ const char* sllbm_step_kernel_name(const sllbm_ctx* c) {
     case kKernelUniform: return "uniform_fused";
     case kKernelPlainF64: return "plain_f64";
     case kKernelMapped: return "mapped_fused";
+    case kKernelQ9: return "d2q9";
     default: return "gather";
   }
 }
@@ -1078,6 +1096,7 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
 sllbm_status sllbm_init_equilibrium_vjp(sllbm_ctx* c, const double* rho, const double* u, const double* v,
                                         const double* T, const float* lam0, float* du, float* dv) {
   if (!c || !rho || !u || !v || !T || !lam0 || !du || !dv) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  if (c->nq1 != kQ1) return fail(c, SLLBM_ERR_UNSUPPORTED, "the equilibrium VJP covers the D2Q25 set");
   InitVjpArgs a{};
   a.rho = rho;
   a.u = u;

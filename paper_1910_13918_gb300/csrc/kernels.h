@@ -89,6 +89,9 @@ cudaError_t launch_step_uniform(const StepArgs& a, const UniformTables& t, int s
 int uniform_tile_rows(int P, bool tall);
 // Plain FP64 step on full populations.
 cudaError_t launch_step_plain_f64(const StepArgs& a, cudaStream_t s);
+// D2Q9 step (isothermal, one population, planar storage): FP32 arithmetic on FP32/BF16
+// deviations or FP64 on full populations; per-axis tables or, with a.mapped, descriptors.
+cudaError_t launch_step_q9(const StepArgs& a, int store, cudaStream_t s);
 
 // ---- precompute (FP64) ----
 struct GeomArgs {
@@ -120,11 +123,11 @@ struct InitArgs {
   int store;
 };
 cudaError_t launch_init_equilibrium(const InitArgs& a, cudaStream_t s);
-// Dense [npop][25][ny][nx] <-> internal layout (interior origin `internal`), element size `elem`,
-// for the dense planes [plane0, plane0 + nplanes) (plane = pop * 25 + velocity).
+// Dense [npop][nq][ny][nx] <-> internal layout (interior origin `internal`), element size `elem`,
+// for the dense planes [plane0, plane0 + nplanes) (plane = pop * nq + velocity).
 cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int plane0,
-                                 int nplanes, int nx, int ny, int pitch, size_t plane_stride, int xs,
-                                 ptrdiff_t ps, cudaStream_t s);
+                                 int nplanes, int nq, int nx, int ny, int pitch, size_t plane_stride,
+                                 int xs, ptrdiff_t ps, cudaStream_t s);
 // Copy the periodic images of interior vertices into the ghost cells of `planes` planes (clamped
 // copies on non-periodic axes).  `origin`: interior origin of plane 0; elem: bytes per element.
 cudaError_t launch_ghost_fill(void* origin, int elem, size_t plane_stride, int pitch, int planes,

@@ -19,8 +19,9 @@ __global__ void __launch_bounds__(kMomThreads) moments_kernel(const __grid_const
     const size_t o = (size_t)iy * a.pitch + (size_t)ix * a.xs;
     const int npop = a.cp.npop;
     double rho = 0.0, jx = 0.0, jy = 0.0, e2 = 0.0;
-    for (int i = 0; i < kQ; ++i) {
-      const double cx = a.cs.xi[i / 5], cy = a.cs.xi[i % 5];
+    const int nq1 = a.cs.nq1;
+    for (int i = 0; i < nq1 * nq1; ++i) {
+      const double cx = a.cs.xi[i / nq1], cy = a.cs.xi[i % nq1];
       double fv, gv = 0.0;
       if (Store == kStoreF64) {
         const double* s = static_cast<const double*>(a.src);
@@ -176,6 +177,7 @@ extern "C" sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, in
   const double s10 = sqrt(10.0), sm = sqrt(5.0 - s10), lg = sqrt(5.0 + s10);
   const double xi[5] = {0.0, sm, lg, -sm, -lg};
   for (int k = 0; k < 5; ++k) a.cs.xi[k] = xi[k];
+  a.cs.nq1 = kQ1;                 // the D2Q25 set
   a.cp.cv = cv;
   a.cp.npop = (cv == 1.0) ? 1 : 2;
   a.store = kStoreF32;

@@ -7,13 +7,13 @@ namespace sllbm {
 
 // ------------------------------------------------------------------------------------------
 // Uniform grids: the departure of vertex j along one axis for velocity component c is
-// x_j - dt xi_c; it depends on (c, j) only, so each axis gets a table [5][nv] of the stencil
+// x_j - dt xi_c; it depends on (c, j) only, so each axis gets a table [nq1][nv] of the stencil
 // start offset (start - j) and p+1 Lagrange weights.
 // ------------------------------------------------------------------------------------------
 template <int P>
 __global__ void axis_table_kernel(AxisK ax, Consts cs, double dt, int* off, float* w32, double* w64) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= kQ1 * ax.nv) return;
+  if (t >= cs.nq1 * ax.nv) return;
   const int c = t / ax.nv, j = t % ax.nv;
   const double x = vertex_ref_coord(j, ax);
   const double xd = fold_axis(x - dt * cs.xi[c], ax);
@@ -37,7 +37,7 @@ __global__ void axis_table_kernel(AxisK ax, Consts cs, double dt, int* off, floa
 
 cudaError_t launch_axis_tables(const AxisK& ax, const Consts& cs, double dt, int* off, float* w32,
                                double* w64, cudaStream_t s) {
-  const int n = kQ1 * ax.nv, threads = 128, blocks = (n + threads - 1) / threads;
+  const int n = cs.nq1 * ax.nv, threads = 128, blocks = (n + threads - 1) / threads;
   switch (ax.p) {
     case 1: axis_table_kernel<1><<<blocks, threads, 0, s>>>(ax, cs, dt, off, w32, w64); break;
     case 2: axis_table_kernel<2><<<blocks, threads, 0, s>>>(ax, cs, dt, off, w32, w64); break;
@@ -67,14 +67,15 @@ __device__ __forceinline__ void vertex_physical(const GeomArgs& g, int ix, int i
 __global__ void descriptor_kernel(const __grid_constant__ GeomArgs g, int* dcx, int* dcy, float* dr,
                                   float* ds, double* dr64, double* ds64) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)kQ * g.nv) return;
+  const int nq1 = g.cs.nq1;
+  if (t >= (long long)nq1 * nq1 * g.nv) return;
   const int i = (int)(t / g.nv);
   const long long v = t % g.nv;
   const int ix = (int)(v % g.nx), iy = (int)(v / g.nx);
   double x, y;
   vertex_physical(g, ix, iy, &x, &y);
-  const double xd = fold_axis(x - g.dt * g.cs.xi[i / 5], g.ax);
-  const double yd = fold_axis(y - g.dt * g.cs.xi[i % 5], g.ay);
+  const double xd = fold_axis(x - g.dt * g.cs.xi[i / nq1], g.ax);
+  const double yd = fold_axis(y - g.dt * g.cs.xi[i % nq1], g.ay);
   double ex = xd, ey = yd;
   if (g.map.kind == 1) {
     bool conv = false;
@@ -109,7 +110,7 @@ __global__ void descriptor_kernel(const __grid_constant__ GeomArgs g, int* dcx, 
 
 cudaError_t launch_descriptors(const GeomArgs& g, int* dcx, int* dcy, float* dr, float* ds,
                                double* dr64, double* ds64, cudaStream_t s) {
-  const long long n = (long long)kQ * g.nv;
+  const long long n = (long long)g.cs.nq1 * g.cs.nq1 * g.nv;
   const int threads = 128;
   descriptor_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(g, dcx, dcy, dr, ds,
                                                                                 dr64, ds64);
@@ -227,9 +228,10 @@ __global__ void init_eq_kernel(const __grid_constant__ InitArgs a) {
   EqFactors<double> e;
   eq_factors<double>(a.cs.he, ux, uy, q, e);
   const size_t o = (size_t)iy * a.pitch + (size_t)ix * a.xs;
-  for (int ia = 0; ia < kQ1; ++ia)
-    for (int ib = 0; ib < kQ1; ++ib) {
-      const int i = 5 * ia + ib;
+  const int nq1 = a.cs.nq1;
+  for (int ia = 0; ia < nq1; ++ia)
+    for (int ib = 0; ib < nq1; ++ib) {
+      const int i = nq1 * ia + ib;
       const double w = a.cs.w[ia] * a.cs.w[ib];
       const double em1 = eq_em1<double>(e, ia, ib);
       const double devf = (rho - 1.0) + rho * em1;          // f^eq / w - 1
@@ -320,17 +322,18 @@ cudaError_t launch_ghost_fill(void* origin, int elem, size_t plane_stride, int p
 }
 
 // ------------------------------------------------------------------------------------------
-// Dense [npop][25][ny][nx] <-> internal layout (ghost cells, row pitch, interleaved pairs).
+// Dense [npop][nq][ny][nx] <-> internal layout (ghost cells, row pitch, interleaved pairs).
 // ------------------------------------------------------------------------------------------
 template <typename E>
 __global__ void state_convert_kernel(const E* src, E* dst, int to_internal, int plane0, int nplanes,
-                                     int nx, int ny, int pitch, size_t plane_stride, int xs, ptrdiff_t ps) {
+                                     int nq, int nx, int ny, int pitch, size_t plane_stride, int xs,
+                                     ptrdiff_t ps) {
   const long long nv = (long long)nx * ny;
   const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t0 >= (long long)nplanes * nv) return;
   const long long t = t0 + (long long)plane0 * nv;   // index in the dense layout
   const long long pl = t / nv, v = t - pl * nv;
-  const int pop = (int)(pl / kQ), i = (int)(pl - (long long)pop * kQ);
+  const int pop = (int)(pl / nq), i = (int)(pl - (long long)pop * nq);
   const int x = (int)(v % nx), y = (int)(v / nx);
   const ptrdiff_t o = (ptrdiff_t)i * plane_stride + pop * ps + (ptrdiff_t)y * pitch + (ptrdiff_t)x * xs;
   if (to_internal)
@@ -340,8 +343,8 @@ __global__ void state_convert_kernel(const E* src, E* dst, int to_internal, int 
 }
 
 cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int plane0,
-                                 int nplanes, int nx, int ny, int pitch, size_t plane_stride, int xs,
-                                 ptrdiff_t ps, cudaStream_t s) {
+                                 int nplanes, int nq, int nx, int ny, int pitch, size_t plane_stride,
+                                 int xs, ptrdiff_t ps, cudaStream_t s) {
   const long long n = (long long)nplanes * nx * ny;
   if (n == 0) return cudaSuccess;
   const int threads = 256;
@@ -350,15 +353,15 @@ cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, i
   switch (elem) {
     case 2:
       state_convert_kernel<uint16_t><<<blocks, threads, 0, s>>>(static_cast<const uint16_t*>(src),
-          static_cast<uint16_t*>(dst), ti, plane0, nplanes, nx, ny, pitch, plane_stride, xs, ps);
+          static_cast<uint16_t*>(dst), ti, plane0, nplanes, nq, nx, ny, pitch, plane_stride, xs, ps);
       break;
     case 4:
       state_convert_kernel<uint32_t><<<blocks, threads, 0, s>>>(static_cast<const uint32_t*>(src),
-          static_cast<uint32_t*>(dst), ti, plane0, nplanes, nx, ny, pitch, plane_stride, xs, ps);
+          static_cast<uint32_t*>(dst), ti, plane0, nplanes, nq, nx, ny, pitch, plane_stride, xs, ps);
       break;
     case 8:
       state_convert_kernel<uint64_t><<<blocks, threads, 0, s>>>(static_cast<const uint64_t*>(src),
-          static_cast<uint64_t*>(dst), ti, plane0, nplanes, nx, ny, pitch, plane_stride, xs, ps);
+          static_cast<uint64_t*>(dst), ti, plane0, nplanes, nq, nx, ny, pitch, plane_stride, xs, ps);
       break;
     default: return cudaErrorInvalidValue;
   }

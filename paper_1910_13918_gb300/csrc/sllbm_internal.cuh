@@ -14,6 +14,8 @@ constexpr int kQ1 = 5;   // D1Q5
 constexpr int kQ = 25;   // D2Q25
 
 // Velocity set (Sec. II.B, Table I) and the 1D Hermite table he[k][a] = He_k(xi_a) / k!.
+// nq1 = 5 (D1Q5, the method's set) or 3 (D1Q3: the D2Q9 set of the comparison in Sec. III.A,
+// nodes 0, +sqrt3, -sqrt3 in the first three entries; the arrays keep the D1Q5 size).
 // The fourth-order equilibrium of Sec. II.A factorises over the two axes:
 //   f_ab^eq = w_a w_b rho sum_{k+l<=4} A_k(u_x) he[k][a] * A_l(u_y) he[l][b]
 // with A_0 = 1, A_1 = u, A_2 = u^2 + q, A_3 = u^3 + 3uq, A_4 = u^4 + 6u^2 q + 3q^2, q = theta - 1
@@ -23,6 +25,7 @@ struct Consts {
   double xi[kQ1], w[kQ1];
   double he[kQ1][kQ1];
   float xif[kQ1], wf[kQ1], hef[kQ1][kQ1];
+  int nq1;   // 1D nodes of the set: 5 (D2Q25) or 3 (D2Q9); velocity i = nq1 a + b
 };
 
 // One axis of the grid as the kernels see it (Sec. II.E): n_cells cells of order p on [lo, hi].

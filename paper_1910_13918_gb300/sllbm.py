@@ -19,6 +19,8 @@ BC_PERIODIC, BC_ZERO_GRADIENT = 0, 1
 NODES_GLC, NODES_EQUIDISTANT = 0, 1
 MAP_IDENTITY, MAP_SINE = 0, 1
 PREC_F32, PREC_BF16_STORE, PREC_F64_PLAIN = 0, 1, 2
+VEL_D2Q25, VEL_D2Q9 = 0, 1
+VELSETS = {"d2q25": VEL_D2Q25, "d2q9": VEL_D2Q9}
 PRECISIONS = {"f32": PREC_F32, "bf16": PREC_BF16_STORE, "f64": PREC_F64_PLAIN}
 
 # every exported symbol of include/sllbm.h
@@ -108,7 +110,7 @@ class SLLBM:
 
     def __init__(self, *, nx_cells, ny_cells, order, x0, x1, y0, y1, bc_x, bc_y, dt, tau, cv,
                  prec="f32", nodes=NODES_GLC, map_kind=MAP_IDENTITY, map_a=0.0, pr=1.0,
-                 isothermal=False, stream=None):
+                 isothermal=False, velset="d2q25", stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("SLLBM needs a CUDA device; there is no CPU path")
@@ -117,7 +119,8 @@ class SLLBM:
         self.prec = prec
         g = GridDesc(nx_cells, ny_cells, order, x0, x1, y0, y1, bc_x, bc_y, nodes, map_kind,
                      (ctypes.c_double * 4)(map_a, 0.0, 0.0, 0.0))
-        p = Params(0, dt, tau, cv, 1.0, PRECISIONS[prec], pr, int(bool(isothermal)))
+        p = Params(VELSETS[velset], dt, tau, cv, 1.0, PRECISIONS[prec], pr, int(bool(isothermal)))
+        self.nq = 9 if velset == "d2q9" else 25
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         self._check(self.lib.sllbm_create(ctypes.byref(g), ctypes.byref(p),
@@ -137,7 +140,7 @@ class SLLBM:
                    y0=w.y0, y1=w.y1, bc_x=w.bc_x, bc_y=w.bc_y, dt=w.dt, tau=w.tau, cv=w.cv,
                    prec=prec, nodes=NODES_GLC if w.nodes == "glc" else NODES_EQUIDISTANT,
                    map_kind=MAP_SINE if w.map_a else MAP_IDENTITY, map_a=w.map_a, pr=w.pr,
-                   isothermal=w.isothermal, stream=stream)
+                   isothermal=w.isothermal, velset=w.velset, stream=stream)
 
     # -- plumbing -------------------------------------------------------------------------------
     def _check(self, status, ctx="self"):
@@ -222,7 +225,7 @@ class SLLBM:
 
     def get_state(self, out=None):
         if out is None:
-            out = self.torch.empty((self.npop, 25, self.ny, self.nx), dtype=self.state_dtype,
+            out = self.torch.empty((self.npop, self.nq, self.ny, self.nx), dtype=self.state_dtype,
                                    device=self.device)
         self._check(self.lib.sllbm_get_state(self.h, _ptr(out)))
         return out

@@ -54,6 +54,7 @@ class Workload:
     cv: float = CV
     pr: float = 1.0                # Prandtl number (1: plain BGK, Sec. II.C)
     isothermal: bool = False       # theta = 1 in the equilibrium (Sec. III.A); needs cv = 1
+    velset: str = "d2q25"          # "d2q25", or "d2q9" (the comparison set of Sec. III.A)
     nodes: str = "glc"
     seed: int = 0
     extra: dict = dataclasses.field(default_factory=dict)
@@ -73,7 +74,15 @@ class Workload:
 
     @property
     def updates_per_step(self):
-        return self.n_vertices * 25 * 2
+        return self.n_vertices * self.n_velocities * self.n_populations
+
+    @property
+    def n_velocities(self):
+        return 9 if self.velset == "d2q9" else 25
+
+    @property
+    def n_populations(self):
+        return 1 if self.cv == 1.0 else 2
 
     @property
     def velocity_scale(self):
@@ -347,12 +356,13 @@ def svi_pr():
     return w
 
 
-def tgv_moving(points=32, ma_h=0.05):
+def tgv_moving(points=32, ma_h=0.05, velset="d2q25"):
     """Isothermal moving Taylor-Green vortex (Sec. III.A) on [0, 2 pi]^2, p = 4, points x points
     vertices: Ma_v = 0.01 (u_v = 0.01, c_s = 1), horizontal Mach number Ma_h, Re = u_v 2 pi / nu
     = 10, compared at the time the vortex speed has decayed to 0.1 u_v.  The paper's time steps
     (0.0008 at 16 points, halved per refinement) are in its unit of time, where u_v = 1: in
-    lattice units dt = 0.0008 / u_v = 0.08 at 16 points, and the end time 1.83 is 183."""
+    lattice units dt = 0.0008 / u_v = 0.08 at 16 points, and the end time 1.83 is 183.
+    ``velset`` "d2q9" runs the comparison set of the same study."""
     uv = 0.01
     nu = uv * 2.0 * math.pi / 10.0
     t_end = math.log(10.0) / (2.0 * nu)          # exp(-2 nu t) = 0.1
@@ -360,9 +370,10 @@ def tgv_moving(points=32, ma_h=0.05):
     steps = steps0 * (points // 16)
     dt = t_end / steps
     L = 2.0 * math.pi
-    return Workload(f"tgvm{points}_p4_mah{ma_h:g}", points // 4, points // 4, 4, 0.0, L, 0.0, L,
+    tag = "" if velset == "d2q25" else f"_{velset}"
+    return Workload(f"tgvm{points}_p4_mah{ma_h:g}{tag}", points // 4, points // 4, 4, 0.0, L, 0.0, L,
                     PERIODIC, PERIODIC, dt, nu / dt + 0.5, steps, "tgvm", cv=1.0, isothermal=True,
-                    seed=8, extra={"u_v": uv, "u_h": ma_h, "nu": nu, "t_end": t_end})
+                    velset=velset, seed=8, extra={"u_v": uv, "u_h": ma_h, "nu": nu, "t_end": t_end})
 
 
 def sdp(points=16, step_factor=1):
@@ -385,4 +396,6 @@ def sdp(points=16, step_factor=1):
 
 ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
        "riemann_paper": riemann_paper, "svi": svi, "svi_pr": svi_pr, "sdp": sdp,
-       "tgv_moving": tgv_moving}
+       "tgv_moving": tgv_moving,
+       # the moving vortex on 2048 x 2048 vertices (state larger than L2), both velocity sets
+       "tgvm2048": lambda: tgv_moving(2048, 0.05), "tgvm2048_d2q9": lambda: tgv_moving(2048, 0.05, "d2q9")}

@@ -23,8 +23,9 @@ def oracle_state(w: W.Workload, nsteps, perturb=True):
     """Oracle post-collision populations (f, g) after nsteps, each (25, ny, nx) float64."""
     grid = oracle_grid(w)
     X, Y = grid.coords()
-    f, g = o.initial_state(*w.fields(X, Y, perturb=perturb), w.cv)
-    return o.run(f, g, o.Departures(grid, w.dt), w.tau, w.cv, nsteps, w.pr, w.isothermal)
+    q = w.n_velocities
+    f, g = o.initial_state(*w.fields(X, Y, perturb=perturb), w.cv, q)
+    return o.run(f, g, o.Departures(grid, w.dt, q=q), w.tau, w.cv, nsteps, w.pr, w.isothermal)
 
 
 def oracle_run(w: W.Workload, nsteps, perturb=True):
@@ -54,6 +55,11 @@ class SparseField:
     def dtype(self):
         return self.values.dtype
 
+    @property
+    def shape(self):
+        """Leading (velocity) axis only: the vertex axes are sparse."""
+        return self.values.shape[:1]
+
 
 def oracle_step_at(w: W.Workload, vertices, perturb=True):
     """Oracle (rho, u, v, theta) after ONE step at the given flat vertex indices only.
@@ -63,9 +69,10 @@ def oracle_step_at(w: W.Workload, vertices, perturb=True):
     """
     grid = oracle_grid(w)
     X, Y = grid.coords()
-    dep = o.Departures(grid, w.dt, vertices)
+    q = w.n_velocities
+    dep = o.Departures(grid, w.dt, vertices, q=q)
     keys = []
-    for i in range(25):
+    for i in range(q):
         for b in range(grid.p + 1):
             jy = grid.ay.vertex_of(dep.cy[i], b)
             for a in range(grid.p + 1):
@@ -74,7 +81,7 @@ def oracle_step_at(w: W.Workload, vertices, perturb=True):
     keys = np.unique(np.concatenate(keys))
     fields = w.fields(X, Y, perturb=perturb)
     sub = [np.asarray(F).reshape(-1)[keys] for F in fields]
-    f0, g0 = o.initial_state(*sub, w.cv)
+    f0, g0 = o.initial_state(*sub, w.cv, q)
     fpre = o.stream(SparseField(grid.nx, keys, f0), dep)
     gpre = o.stream(SparseField(grid.nx, keys, g0), dep)
     f1, g1 = o.collide(fpre, gpre, w.tau, w.cv, w.pr, w.isothermal)

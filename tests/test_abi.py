@@ -67,7 +67,11 @@ def test_host_validation_of_sizes_and_options():
                                  ("isothermal", 1, sllbm.ERR_ARG),      # needs cv = 1
                                  ("isothermal", 2, sllbm.ERR_ARG), ("T0", 2.0, sllbm.ERR_ARG),
                                  ("dt", 0.0, sllbm.ERR_ARG), ("cv", 0.5, sllbm.ERR_ARG),
-                                 ("velset", 1, sllbm.ERR_UNSUPPORTED), ("prec", 9, sllbm.ERR_ARG)):
+                                 ("velset", 1, sllbm.ERR_UNSUPPORTED),   # D2Q9: isothermal only
+                                 ("velset", 2, sllbm.ERR_UNSUPPORTED), ("prec", 9, sllbm.ERR_ARG)):
         p = ok_params()
         setattr(p, field, value)
         assert create(ok_grid(), p) == status, (field, value)
+    # D2Q9 with the isothermal configuration but a Prandtl number other than 1
+    p = sllbm.Params(sllbm.VEL_D2Q9, 0.01, 0.8, 1.0, 1.0, 0, 0.75, 1)
+    assert create(ok_grid(), p) == sllbm.ERR_UNSUPPORTED

@@ -1,0 +1,131 @@
+"""The D2Q9 velocity set (the comparison set of Sec. III.A) on the GPU, through the C ABI.
+
+Parity with the oracle at the tolerances of the D2Q25 paths (FP32 <= 1e-5 after one step and
+<= 1e-4 after 100, FP64 populations <= 1e-11 of the largest), on a uniform periodic grid, a
+uniform zero-gradient grid and a transformed grid; then the study of Sec. III.A itself: with the
+vortex at rest both sets converge with the grid, while moving the vortex at Ma_h = 0.05 leaves
+D2Q9 with an error that no longer converges (its equilibrium misses the u^3 term of the third
+moment) and D2Q25 as accurate as at rest.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_1910_13918_gb300 import workloads as W
+
+from . import helpers as H
+from .test_gpu_parity import TOL_1, TOL_100, TOL_F64, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    periodic = W.tgv_moving(16, 0.05, "d2q9")
+    clamped = dataclasses.replace(periodic, name="tgvm_d2q9_clamped", bc_x=W.ZERO_GRADIENT,
+                                  bc_y=W.ZERO_GRADIENT, nx_cells=5, ny_cells=3)
+    # the sine map needs the reference box [0, 2] x [0, 1]; vortex fields over that box
+    mapped = dataclasses.replace(periodic, name="tgvm_d2q9_mapped", x0=0.0, x1=2.0, y0=0.0, y1=1.0,
+                                 bc_x=W.ZERO_GRADIENT, bc_y=W.PERIODIC, nx_cells=6, ny_cells=3,
+                                 map_a=0.05, dt=0.01)
+    return {"periodic": periodic, "clamped": clamped, "mapped": mapped}
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("nsteps,tol", [(1, TOL_1), (100, TOL_100)])
+def test_d2q9_parity_f32(gpu_lib, name, nsteps, tol):
+    w = CASES[name]
+    s, gpu, _ = gpu_run(w, nsteps, "f32")
+    assert s.kernel_name == "d2q9" and s.npop == 1 and s.nq == 9
+    err = H.field_errors(gpu, H.oracle_run(w, nsteps), w.velocity_scale)
+    assert max(err.values()) <= tol, (name, err)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_d2q9_parity_f64_state(gpu_lib, name):
+    w = CASES[name]
+    s, _, _ = gpu_run(w, 20, "f64")
+    st = s.get_state().cpu().numpy()
+    assert st.shape == (1, 9, w.ny, w.nx)
+    f, _ = H.oracle_state(w, 20)
+    assert np.max(np.abs(st[0] - f)) <= TOL_F64 * np.max(np.abs(f))
+
+
+def test_d2q9_bf16_storage(gpu_lib):
+    w = CASES["periodic"]
+    _, gpu, _ = gpu_run(w, 10, "bf16")
+    err = H.field_errors(gpu, H.oracle_run(w, 10), w.velocity_scale)
+    assert max(err["rho"], err["u"], err["v"]) < 3e-2, err
+
+
+def test_d2q9_state_round_trip_and_host_step(gpu_lib):
+    """get_state / set_state / step_host on the [1][9][ny][nx] state."""
+    import torch
+    from paper_1910_13918_gb300.sllbm import SLLBM
+    w = CASES["periodic"]
+    s = SLLBM.from_workload(w, prec="f32")
+    s.precompute()
+    x, y = (t.cpu().numpy() for t in s.coords())
+    s.init(*w.fields(x, y, perturb=True))
+    assert s.state_bytes == 9 * w.n_vertices * 4
+    st = s.get_state()
+    s.step(1)
+    after = s.get_state()
+    s.set_state(st)
+    h_in = st.cpu().numpy().copy()
+    h_out = np.empty_like(h_in)
+    s.step_host(h_in, h_out, 1)
+    assert np.array_equal(h_out, after.cpu().numpy())
+    torch.cuda.synchronize()
+
+
+def test_d2q9_rejects_what_it_does_not_carry(gpu_lib):
+    from paper_1910_13918_gb300.sllbm import SLLBM, SLLBMError, ERR_UNSUPPORTED
+    w = CASES["periodic"]
+    for bad in (dict(isothermal=False), dict(pr=0.75)):
+        with pytest.raises(SLLBMError) as e:
+            SLLBM.from_workload(dataclasses.replace(w, **bad))
+        assert e.value.status == ERR_UNSUPPORTED
+
+
+def _error(w, prec="f64"):
+    from paper_1910_13918_gb300.sllbm import SLLBM
+    s = SLLBM.from_workload(w, prec=prec)
+    s.precompute()
+    x, y = (t.cpu().numpy() for t in s.coords())
+    s.init(*w.fields(x, y))
+    m0 = s.moments()["mass"]
+    s.step(w.steps)
+    m = s.moments()
+    ur, vr, _ = W.tgvm_reference(w, x, y, w.extra["t_end"])
+    err = max(np.abs(m["u"].double().cpu().numpy() - ur).max(),
+              np.abs(m["v"].double().cpu().numpy() - vr).max())
+    return err / (0.1 * w.extra["u_v"]), m["mass"] / m0 - 1
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_galilean_invariance_d2q9_against_d2q25(gpu_lib, prec):
+    """Sec. III.A, Fig. tgv: at rest D2Q9 and D2Q25 both converge with the grid, D2Q25 two to
+    three times less accurate (more interpolations per step); moving at Ma_h = 0.05, D2Q9
+    converges towards a velocity-set error while D2Q25 keeps its error at rest."""
+    err = {}
+    for vs in ("d2q9", "d2q25"):
+        for n in (32, 64):
+            for mah in (0.0, 0.05):
+                e, dm = _error(W.tgv_moving(n, mah, vs), prec)
+                err[vs, n, mah] = e
+                assert abs(dm) < 1e-6, (vs, n, mah, dm)
+    print("moving Taylor-Green errors:", {k: f"{v:.3e}" for k, v in err.items()})
+    for vs in ("d2q9", "d2q25"):
+        assert np.log2(err[vs, 32, 0.0] / err[vs, 64, 0.0]) > 2.5, err   # converges at rest
+    for n in (32, 64):
+        assert 1.5 < err["d2q25", n, 0.0] / err["d2q9", n, 0.0] < 4.0, err
+    # D2Q9 moving: far above its error at rest, and refinement no longer helps much
+    assert err["d2q9", 64, 0.05] > 4 * err["d2q9", 64, 0.0], err
+    assert np.log2(err["d2q9", 32, 0.05] / err["d2q9", 64, 0.05]) < 1.5, err
+    # D2Q25 moving: as accurate as at rest, and well below D2Q9 moving
+    assert err["d2q25", 64, 0.05] < 1.25 * err["d2q25", 64, 0.0], err
+    assert err["d2q25", 64, 0.05] < 0.25 * err["d2q9", 64, 0.05], err
