@@ -7,14 +7,15 @@
 // invariance that the comparison shows).
 //
 // One population (the isothermal configuration) in planar storage, velocity i = 3a + b:
-// FP32 / BF16 deviations f_i - w_i with FP32 arithmetic, or FP64 full populations.  One thread
-// per vertex gathers the (p+1)^2 stencil of each of the 9 planes through L1/L2 -- with 9 values
-// a vertex the tile reuse of shared-memory staging buys little -- then collides in registers.
-// Uniform grids read the per-axis tables, transformed grids the per-(velocity, vertex) cells and
-// local coordinates.
+// FP32 / BF16 deviations f_i - w_i with FP32 arithmetic, or FP64 full populations.  Uniform
+// grids in FP32 / BF16 run the tiled kernel below (shared-memory windows, sum factorisation);
+// transformed grids, FP64, and uniform grids whose departures reach farther than its window run
+// the gather kernel: one thread per vertex reads the (p+1)^2 stencil of each of the 9 planes
+// through L1/L2 (per-axis tables, or the per-(velocity, vertex) cells and local coordinates).
 #include <type_traits>
 
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace sllbm {
 
@@ -95,6 +96,44 @@ __device__ __forceinline__ T eq9_em1(const Eq9<T>& e, int a, int b) {
   return s;
 }
 
+// BGK of one vertex in deviation form, FP32: fb[i] = f_i - w_i before, the post-collision
+// deviations after.  Returns false if the density is non-positive or a value is not finite.
+__device__ __forceinline__ bool collide_q9_f32(float (&fb)[kN], const Consts& cs, const CollideK& cp) {
+  float drho = 0.f, jx = 0.f, jy = 0.f;
+#pragma unroll
+  for (int i = 0; i < kN; ++i) {   // sum w = 1 and sum w xi = 0: the moments of fbar
+    drho += fb[i];
+    jx += fb[i] * cs.xif[i / kN1];
+    jy += fb[i] * cs.xif[i % kN1];
+  }
+  const float rho = 1.f + drho;
+  const float ux = jx / rho, uy = jy / rho;
+  Eq9<float> e;
+  eq9_factors<float>(cs.hef, ux, uy, e);
+  const float om = cp.omegaf;
+  // relax, and sum the residual moments of (f^eq - f) to restore mass and momentum to the
+  // rounding of those sums (as in the D2Q25 kernels)
+  float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < kN; ++i) {
+    const int ia = i / kN1, ib = i % kN1;
+    const float w = cs.wf[ia] * cs.wf[ib];
+    const float d = w * (drho + rho * eq9_em1<float>(e, ia, ib)) - fb[i];
+    r0 += d;
+    r1 += d * cs.xif[ia];
+    r2 += d * cs.xif[ib];
+    fb[i] = fmaf(om, d, fb[i]);
+  }
+  // remove om (r0 + r1 xi_x + r2 xi_y) w_i: sum w = 1, sum w xi xi = I on D2Q9
+#pragma unroll
+  for (int i = 0; i < kN; ++i) {
+    const int ia = i / kN1, ib = i % kN1;
+    const float w = cs.wf[ia] * cs.wf[ib];
+    fb[i] -= om * w * (r0 + r1 * cs.xif[ia] + r2 * cs.xif[ib]);
+  }
+  return rho > 0.f && isfinite(rho) && isfinite(ux) && isfinite(uy);
+}
+
 template <int P, typename Store, bool Mapped>
 __global__ void __launch_bounds__(128) step_q9_kernel(const __grid_constant__ StepArgs a) {
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -170,45 +209,263 @@ __global__ void __launch_bounds__(128) step_q9_kernel(const __grid_constant__ St
       for (int kb = 1; kb <= P; ++kb) acc = fmaf(wy[kb], rows[kb] - rows[0], acc);
       fb[i] = acc;
     }
-    float drho = 0.f, jx = 0.f, jy = 0.f;
+    const bool ok = collide_q9_f32(fb, a.cs, a.cp);
 #pragma unroll
-    for (int i = 0; i < kN; ++i) {   // sum w = 1 and sum w xi = 0: the moments of fbar
-      drho += fb[i];
-      jx += fb[i] * a.cs.xif[i / kN1];
-      jy += fb[i] * a.cs.xif[i % kN1];
-    }
-    const float rho = 1.f + drho;
-    const float ux = jx / rho, uy = jy / rho;
-    Eq9<float> e;
-    eq9_factors<float>(a.cs.hef, ux, uy, e);
-    const float om = a.cp.omegaf;
-    // relax, and sum the residual moments of (f^eq - f) to restore mass and momentum to the
-    // rounding of those sums (as in the D2Q25 kernels)
-    float r0 = 0.f, r1 = 0.f, r2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < kN; ++i) {
-      const int ia = i / kN1, ib = i % kN1;
-      const float w = a.cs.wf[ia] * a.cs.wf[ib];
-      const float d = w * (drho + rho * eq9_em1<float>(e, ia, ib)) - fb[i];
-      r0 += d;
-      r1 += d * a.cs.xif[ia];
-      r2 += d * a.cs.xif[ib];
-      fb[i] = fmaf(om, d, fb[i]);
-    }
-    // remove om (r0 + r1 xi_x + r2 xi_y) w_i: sum w = 1, sum w xi xi = I on D2Q9
-#pragma unroll
-    for (int i = 0; i < kN; ++i) {
-      const int ia = i / kN1, ib = i % kN1;
-      const float w = a.cs.wf[ia] * a.cs.wf[ib];
-      const float val = fb[i] - om * w * (r0 + r1 * a.cs.xif[ia] + r2 * a.cs.xif[ib]);
-      st_store(dst + (size_t)i * a.plane_stride + o, val);
-    }
-    if (!(rho > 0.f && isfinite(rho) && isfinite(ux) && isfinite(uy))) atomicOr(a.flag, 1);
+    for (int i = 0; i < kN; ++i) st_store(dst + (size_t)i * a.plane_stride + o, fb[i]);
+    if (!ok) atomicOr(a.flag, 1);
   }
+}
+
+// Uniform grids, FP32 arithmetic: tiles of 32 x kTY vertices, one thread each.  Plane by plane,
+// the source window that the tile's stencils reach is staged in shared memory (coalesced loads;
+// the next plane's window is loaded into registers while the current one is interpolated), then
+// interpolated along y for every staged column with the taps of the tile row (warp r takes row
+// r), and along x for every vertex with its own taps: the sum factorisation of the
+// tensor-product stencil, 2(p+1) taps a value instead of (p+1)^2.  The source offsets of the
+// staged elements do not depend on the plane and are formed once per tile.
+constexpr int kTY = 8;                 // tile rows
+constexpr int kNT = 32 * kTY;          // threads: warp r handles tile row r
+constexpr int kRC = 3;                 // window row chunks: row r of the window is read by warp r % kTY
+constexpr int kCC = 3;                 // window column chunks of 32
+constexpr int kMaxW = 32 * kCC, kMaxH = kTY * kRC;
+
+struct Window {
+  int ox, oy;   // window origin relative to the tile origin (the smallest stencil offsets)
+  int W, H;     // window columns (<= kMaxW) and rows (<= kMaxH)
+};
+
+template <int P, typename Store>
+__global__ void __launch_bounds__(kNT) step_q9_tiled_kernel(const __grid_constant__ StepArgs a,
+                                                             const Window win) {
+  __shared__ float S[kMaxH * kMaxW];   // staged window of one plane, [H][W]
+  __shared__ float T[kTY * kMaxW];     // y-interpolated rows, [kTY][W]
+  const int tid = threadIdx.x, lane = tid & 31, row = tid >> 5;
+  const int tiles_x = (a.nx + 31) / 32;
+  const int tx0 = (int)(blockIdx.x % tiles_x) * 32, ty0 = (int)(blockIdx.x / tiles_x) * kTY;
+  const int x = tx0 + lane, y = ty0 + row;
+  const int W = win.W, H = win.H;
+  const Store* src = static_cast<const Store*>(a.src);
+
+  // taps of this thread's column (x pass) and of its warp's row (y pass), clamped into the grid
+  // for threads past its edge; stencil starts as window column / row
+  const int xc = min(x, a.nx - 1), yc = min(y, a.ny - 1);
+  int xo[kN1], yo[kN1];
+  float xw[kN1][P + 1], yw[kN1][P + 1];
+#pragma unroll
+  for (int c = 0; c < kN1; ++c) {
+    xo[c] = xc + a.offx[c * a.nx + xc] - tx0 - win.ox;
+    yo[c] = yc + a.offy[c * a.ny + yc] - ty0 - win.oy;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      xw[c][k] = a.wx[(size_t)(c * a.nx + xc) * (P + 1) + k];
+      yw[c][k] = a.wy[(size_t)(c * a.ny + yc) * (P + 1) + k];
+    }
+  }
+  // the window elements this thread stages: rows row + kTY j, columns lane + 32 m (wrapped or
+  // clamped into the grid), as offsets within a plane
+  size_t grow[kRC];
+  int gcol[kCC];
+#pragma unroll
+  for (int j = 0; j < kRC; ++j) {
+    int gy = ty0 + win.oy + row + kTY * j;
+    gy = a.periodic_y ? wrap_index(gy, a.ny, 1) : min(max(gy, 0), a.ny - 1);
+    grow[j] = (size_t)gy * a.pitch;
+  }
+#pragma unroll
+  for (int m = 0; m < kCC; ++m) {
+    int gx = tx0 + win.ox + lane + 32 * m;
+    gx = a.periodic_x ? wrap_index(gx, a.nx, 1) : min(max(gx, 0), a.nx - 1);
+    gcol[m] = gx;
+  }
+  float pre[kRC][kCC];
+  auto load = [&](int i) {
+    const Store* pl = src + (size_t)i * a.plane_stride;
+#pragma unroll
+    for (int j = 0; j < kRC; ++j)
+#pragma unroll
+      for (int m = 0; m < kCC; ++m)
+        if (row + kTY * j < H && lane + 32 * m < W) pre[j][m] = ld_store(pl + grow[j] + gcol[m]);
+  };
+  load(0);
+  float fb[kN];
+#pragma unroll
+  for (int i = 0; i < kN; ++i) {
+    const int ca = i / kN1, cb = i % kN1;
+    // S is free: every thread is past the previous plane's y pass (second barrier below)
+#pragma unroll
+    for (int j = 0; j < kRC; ++j)
+#pragma unroll
+      for (int m = 0; m < kCC; ++m)
+        if (row + kTY * j < H && lane + 32 * m < W) S[(row + kTY * j) * W + lane + 32 * m] = pre[j][m];
+    if (i + 1 < kN) load(i + 1);
+    __syncthreads();   // window staged; every thread is past the previous plane's x pass (T free)
+#pragma unroll
+    for (int m = 0; m < kCC; ++m) {
+      const int c = lane + 32 * m;
+      if (c < W) {
+        const float* col = S + yo[cb] * W + c;
+        const float base = col[0];
+        float acc = base;
+#pragma unroll
+        for (int k = 1; k <= P; ++k) acc = fmaf(yw[cb][k], col[k * W] - base, acc);
+        T[row * W + c] = acc;
+      }
+    }
+    __syncthreads();   // T complete
+    {
+      const float* t = T + row * W + xo[ca];
+      const float base = t[0];
+      float acc = base;
+#pragma unroll
+      for (int k = 1; k <= P; ++k) acc = fmaf(xw[ca][k], t[k] - base, acc);
+      fb[i] = acc;
+    }
+  }
+  if (x >= a.nx || y >= a.ny) return;
+  const bool ok = collide_q9_f32(fb, a.cs, a.cp);
+  Store* dst = static_cast<Store*>(a.dst) + (size_t)y * a.pitch + x;
+#pragma unroll
+  for (int i = 0; i < kN; ++i) st_store(dst + (size_t)i * a.plane_stride, fb[i]);
+  if (!ok) atomicOr(a.flag, 1);
+}
+
+// FP32 storage: the same tile, with the windows of all 9 planes requested up front by
+// asynchronous 4-byte copies into shared memory (one commit group per plane), so that the
+// interpolation of plane i overlaps the transfer of the later planes.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until the copies of plane i (group i of 9) have landed
+__device__ __forceinline__ void cp_async_wait_plane(int i) {
+  switch (i) {
+    case 0: asm volatile("cp.async.wait_group 8;\n" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 7;\n" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 6;\n" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 5;\n" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;\n" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 3;\n" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 2;\n" ::: "memory"); break;
+    case 7: asm volatile("cp.async.wait_group 1;\n" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 0;\n" ::: "memory"); break;
+  }
+}
+
+size_t async_smem_bytes(const Window& w) { return sizeof(float) * ((size_t)kN * w.H * w.W + (size_t)kTY * w.W); }
+
+template <int P>
+__global__ void __launch_bounds__(kNT) step_q9_async_kernel(const __grid_constant__ StepArgs a,
+                                                             const Window win) {
+  extern __shared__ float q9_smem[];
+  const int W = win.W, H = win.H;
+  float* S = q9_smem;              // [9][H][W] staged windows
+  float* T = S + kN * H * W;       // [kTY][W] y-interpolated rows
+  const int tid = threadIdx.x, lane = tid & 31, row = tid >> 5;
+  const int tiles_x = (a.nx + 31) / 32;
+  const int tx0 = (int)(blockIdx.x % tiles_x) * 32, ty0 = (int)(blockIdx.x / tiles_x) * kTY;
+  const int x = tx0 + lane, y = ty0 + row;
+  const float* src = static_cast<const float*>(a.src);
+  {
+    size_t grow[kRC];
+    int gcol[kCC];
+#pragma unroll
+    for (int j = 0; j < kRC; ++j) {
+      int gy = ty0 + win.oy + row + kTY * j;
+      gy = a.periodic_y ? wrap_index(gy, a.ny, 1) : min(max(gy, 0), a.ny - 1);
+      grow[j] = (size_t)gy * a.pitch;
+    }
+#pragma unroll
+    for (int m = 0; m < kCC; ++m) {
+      int gx = tx0 + win.ox + lane + 32 * m;
+      gx = a.periodic_x ? wrap_index(gx, a.nx, 1) : min(max(gx, 0), a.nx - 1);
+      gcol[m] = gx;
+    }
+#pragma unroll 1
+    for (int i = 0; i < kN; ++i) {
+      const float* pl = src + (size_t)i * a.plane_stride;
+      float* Si = S + i * H * W;
+#pragma unroll
+      for (int j = 0; j < kRC; ++j)
+#pragma unroll
+        for (int m = 0; m < kCC; ++m)
+          if (row + kTY * j < H && lane + 32 * m < W)
+            cp_async4(Si + (row + kTY * j) * W + lane + 32 * m, pl + grow[j] + gcol[m]);
+      cp_async_commit();
+    }
+  }
+  const int xc = min(x, a.nx - 1), yc = min(y, a.ny - 1);
+  int xo[kN1], yo[kN1];
+  float xw[kN1][P + 1], yw[kN1][P + 1];
+#pragma unroll
+  for (int c = 0; c < kN1; ++c) {
+    xo[c] = xc + a.offx[c * a.nx + xc] - tx0 - win.ox;
+    yo[c] = yc + a.offy[c * a.ny + yc] - ty0 - win.oy;
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      xw[c][k] = a.wx[(size_t)(c * a.nx + xc) * (P + 1) + k];
+      yw[c][k] = a.wy[(size_t)(c * a.ny + yc) * (P + 1) + k];
+    }
+  }
+  float fb[kN];
+#pragma unroll
+  for (int i = 0; i < kN; ++i) {
+    const int ca = i / kN1, cb = i % kN1;
+    cp_async_wait_plane(i);
+    __syncthreads();   // plane i staged by every thread; every thread is past the previous x pass
+    const float* Si = S + i * H * W;
+#pragma unroll
+    for (int m = 0; m < kCC; ++m) {
+      const int c = lane + 32 * m;
+      if (c < W) {
+        const float* col = Si + yo[cb] * W + c;
+        const float base = col[0];
+        float acc = base;
+#pragma unroll
+        for (int k = 1; k <= P; ++k) acc = fmaf(yw[cb][k], col[k * W] - base, acc);
+        T[row * W + c] = acc;
+      }
+    }
+    __syncthreads();   // T complete
+    {
+      const float* t = T + row * W + xo[ca];
+      const float base = t[0];
+      float acc = base;
+#pragma unroll
+      for (int k = 1; k <= P; ++k) acc = fmaf(xw[ca][k], t[k] - base, acc);
+      fb[i] = acc;
+    }
+  }
+  if (x >= a.nx || y >= a.ny) return;
+  const bool ok = collide_q9_f32(fb, a.cs, a.cp);
+  float* dst = static_cast<float*>(a.dst) + (size_t)y * a.pitch + x;
+#pragma unroll
+  for (int i = 0; i < kN; ++i) dst[(size_t)i * a.plane_stride] = fb[i];
+  if (!ok) atomicOr(a.flag, 1);
 }
 
 template <int P, typename Store>
 cudaError_t launch_ps(const StepArgs& a, cudaStream_t s) {
+  if constexpr (!std::is_same<Store, double>::value) {
+    // uniform grid whose stencil window fits the staging buffer: the tiled kernel
+    const Window win{a.offx_min, a.offy_min, 32 + a.offx_max - a.offx_min, kTY + a.offy_max - a.offy_min};
+    if (!a.mapped && win.W <= kMaxW && win.H <= kMaxH) {
+      const unsigned tiles = (unsigned)(((a.nx + 31) / 32) * ((a.ny + kTY - 1) / kTY));
+      if constexpr (std::is_same<Store, float>::value) {
+        static bool attr_set = false;   // the largest window needs more than the default 48 KB
+        if (!attr_set) {
+          const Window big{0, 0, kMaxW, kMaxH};
+          const cudaError_t e = cudaFuncSetAttribute(step_q9_async_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)async_smem_bytes(big));
+          if (e != cudaSuccess) return e;
+          attr_set = true;
+        }
+        step_q9_async_kernel<P><<<tiles, kNT, async_smem_bytes(win), s>>>(a, win);
+      } else {
+        step_q9_tiled_kernel<P, Store><<<tiles, kNT, 0, s>>>(a, win);
+      }
+      return cudaGetLastError();
+    }
+  }
   const int threads = 128;
   const unsigned blocks = (unsigned)((a.nv + threads - 1) / threads);
   if (a.mapped)
