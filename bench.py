@@ -31,10 +31,10 @@ UNIT = "GVUPS"
 # DRAM traffic (read + write bytes per launch) of the step kernel from an ncu capture, keyed by
 # (kernel source digest, workload, precision); reported as null once the kernel source changes.
 NCU_TRAFFIC = {
-    # profiles/step_uniform_tgv256_p4_f32.md: 222.5 MB read + 173.8 MB written
-    ("f9c8df6df211fc7b", "tgv256_p4", "f32"): 396.4e6,
-    # profiles/step_mapped_svi512x256_p2_f32.md: 273.8 MB read + 78.8 MB written
-    ("f9c8df6df211fc7b", "svi512x256_p2_mapped", "f32"): 352.6e6,
+    # profiles/step_uniform_tgv256_p4_f32.md: 222.7 MB read + 173.6 MB written
+    ("1b868f3765cab1c8", "tgv256_p4", "f32"): 396.2e6,
+    # profiles/step_mapped_svi512x256_p2_f32.md: 273.8 MB read + 78.4 MB written
+    ("1b868f3765cab1c8", "svi512x256_p2_mapped", "f32"): 352.2e6,
 }
 
 

@@ -451,15 +451,13 @@ cudaError_t launch_ps(const StepArgs& a, cudaStream_t s) {
     if (!a.mapped && win.W <= kMaxW && win.H <= kMaxH) {
       const unsigned tiles = (unsigned)(((a.nx + 31) / 32) * ((a.ny + kTY - 1) / kTY));
       if constexpr (std::is_same<Store, float>::value) {
-        static bool attr_set = false;   // the largest window needs more than the default 48 KB
-        if (!attr_set) {
-          const Window big{0, 0, kMaxW, kMaxH};
-          const cudaError_t e = cudaFuncSetAttribute(step_q9_async_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)async_smem_bytes(big));
+        const size_t smem = async_smem_bytes(win);
+        if (smem > 48 * 1024) {   // wide windows need more than the default dynamic shared memory
+          const cudaError_t e = cudaFuncSetAttribute(step_q9_async_kernel<P>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
           if (e != cudaSuccess) return e;
-          attr_set = true;
         }
-        step_q9_async_kernel<P><<<tiles, kNT, async_smem_bytes(win), s>>>(a, win);
+        step_q9_async_kernel<P><<<tiles, kNT, smem, s>>>(a, win);
       } else {
         step_q9_tiled_kernel<P, Store><<<tiles, kNT, 0, s>>>(a, win);
       }
