@@ -47,6 +47,20 @@ def _kernel_digest():
     return h.hexdigest()[:16]
 
 
+def bytes_per_update(w, prec, kernel):
+    """Algorithmic HBM bytes per update: the stored state read once and written once.  D2Q25
+    FP32/BF16 storage keeps (f, g) pairs (the g slot zero with one population); FP64 and D2Q9
+    keep the populations they have.  The fused mapped kernel also reads the 12-byte departure
+    record of each (velocity, vertex), shared by the populations."""
+    stored = (w.n_velocities * w.n_populations
+              if prec == "f64" or w.velset == "d2q9" else 2 * w.n_velocities)
+    elem = {"f32": 4, "bf16": 2, "f64": 8}[prec]
+    b = 2 * stored * elem / (w.n_velocities * w.n_populations)
+    if kernel == "mapped_fused":
+        b += 12 / w.n_populations
+    return b
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -307,17 +321,7 @@ def run_ours(args):
 
     if rank == 0:
         peaks, src = _peaks()
-        # the stored state read once and written once: D2Q25 FP32/BF16 keeps (f, g) pairs (the g
-        # slot zero with one population), FP64 and D2Q9 keep the populations they have
-        stored = (w.n_velocities * w.n_populations
-                  if args.prec == "f64" or w.velset == "d2q9" else 2 * w.n_velocities)
-        elem = {"f32": 4, "bf16": 2, "f64": 8}[args.prec]
-        bytes_per_update = 2 * stored * elem / (w.n_velocities * w.n_populations)
-        if s.kernel_name == "mapped_fused":
-            # + the departure record of each (velocity, vertex): stencil origin and (r, s), 12 B,
-            # shared by the populations (6 B per update with f and g)
-            bytes_per_update += 12 / w.n_populations
-        alg_bytes = updates * bytes_per_update
+        alg_bytes = updates * bytes_per_update(w, args.prec, s.kernel_name)
         achieved = alg_bytes / (ms_step * 1e-3) / 1e9
         peak = float(peaks.get("hbm_gbs", 6800.0))
         traffic = NCU_TRAFFIC.get((_kernel_digest(), w.name, args.prec))
