@@ -9,6 +9,8 @@ Modules
 -------
 ``sllbm``    velocity set, Hermite equilibrium, grid, departure points, streaming, collision,
              diagnostics (Sec. II of the paper), written as plain loops in float64.
+``sllbm3d``  the same step in three dimensions (D3Q125 on hexahedral cells), reusing the
+             dimension-free parts of ``sllbm``.
 ``adjoint``  reference adjoint of one step: complex-step collision Jacobian and a scatter
              transpose of the interpolation.
 ``riemann``  exact Riemann solver for the Euler equations (validation of the Sod case, Sec. III.C).
