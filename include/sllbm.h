@@ -65,7 +65,7 @@ typedef enum {
  * fourth-order equilibrium (Sec. III.A); isothermal only (params.isothermal = 1, so cv = 1), plain
  * BGK (pr 0 or 1), no adjoint and no equilibrium VJP (UNSUPPORTED otherwise).  Its state is one
  * population in planar storage for every precision. */
-typedef enum { SLLBM_VEL_D2Q25_HERMITE = 0, SLLBM_VEL_D2Q9 = 1 } sllbm_velset;
+typedef enum { SLLBM_VEL_D2Q25_HERMITE = 0, SLLBM_VEL_D2Q9 = 1, SLLBM_VEL_D3Q125 = 2 } sllbm_velset;
 typedef enum {
     SLLBM_PREC_F32 = 0,         /* fused FP32 step, FP32 deviation storage                   */
     SLLBM_PREC_BF16_STORE = 1,  /* fused step with FP32 arithmetic and BF16 deviation storage */
@@ -202,6 +202,53 @@ sllbm_status sllbm_init_equilibrium_vjp(sllbm_ctx* ctx, const double* rho_dev, c
 sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, int ny, double cv,
                                    const double* A_dev, float* rho_dev, float* u_dev, float* v_dev,
                                    float* T_dev, double* mass_energy_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------------------------------------
+ * 3D extension (the step the paper names as its next one): D3Q125, the tensor product of D1Q5
+ * three times, on a uniform grid of hexahedral Lagrange cells of order 1..4 (Sec. II.E per axis),
+ * with the same fourth-order equilibrium (Sec. II.A over index tuples in {x, y, z}^n), g^eq =
+ * (2 C_v - 3) theta f^eq (Sec. II.D) and BGK (Eq. streaming_fg, Pr = 1).  Plain FP64 step on
+ * full populations: params.velset = SLLBM_VEL_D3Q125, params.prec = SLLBM_PREC_F64_PLAIN,
+ * pr 0 or 1, cv >= 3/2 (cv = 3/2 carries f only; isothermal = 1 needs it).  Population field
+ * [n_pop][125][nz][ny][nx], velocity i = 25a + 5b + c (D1Q5 indices of the x, y, z components in
+ * Table I order); vertex arrays [nz][ny][nx].  Conventions otherwise as above.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int nx_cells, ny_cells, nz_cells, order;
+    double x0, x1, y0, y1, z0, z1;
+    int bc_x, bc_y, bc_z;       /* sllbm_bc    */
+    int nodes;                  /* sllbm_nodes */
+} sllbm_grid3_desc;
+
+typedef struct sllbm3d_ctx sllbm3d_ctx;  /* opaque, library-owned */
+
+/* Create / destroy a 3D context.  Errors: ARG, UNSUPPORTED (other velocity set, precision,
+ * Prandtl number, order), OOM, CUDA. */
+sllbm_status sllbm3d_create(const sllbm_grid3_desc* grid, const sllbm_params* params,
+                            void* cuda_stream, sllbm3d_ctx** out);
+sllbm_status sllbm3d_destroy(sllbm3d_ctx* ctx);
+/* Vertex counts per axis and populations carried. */
+sllbm_status sllbm3d_grid_info(const sllbm3d_ctx* ctx, int* nx, int* ny, int* nz, int* n_pop);
+/* Vertex coordinates, FP64 device arrays of nz*ny*nx doubles each. */
+sllbm_status sllbm3d_vertex_coords(sllbm3d_ctx* ctx, double* x_dev, double* y_dev, double* z_dev);
+/* Per-axis departure tables (stencil start and p+1 Lagrange weights per velocity component and
+ * vertex, FP64).  Must precede init and step. */
+sllbm_status sllbm3d_precompute_departures(sllbm3d_ctx* ctx);
+/* Initial state: f^eq and g^eq of (rho, u, v, w, T) (device FP64 arrays of nz*ny*nx). */
+sllbm_status sllbm3d_init_equilibrium(sllbm3d_ctx* ctx, const double* rho_dev, const double* u_dev,
+                                      const double* v_dev, const double* w_dev, const double* T_dev);
+/* Advance nsteps steps (pull interpolation of every velocity with the tensor-product Lagrange
+ * basis, moments, BGK); enqueues only. */
+sllbm_status sllbm3d_step(sllbm3d_ctx* ctx, int nsteps);
+/* rho, u, v, w, T of the current state (FP64 device arrays of nz*ny*nx, each may be NULL);
+ * synchronises; SLLBM_ERR_UNSTABLE if a step or this call saw a non-positive or non-finite
+ * density or temperature. */
+sllbm_status sllbm3d_moments(sllbm3d_ctx* ctx, double* rho_dev, double* u_dev, double* v_dev,
+                             double* w_dev, double* T_dev);
+/* Copy the state to / from a caller-owned device buffer of n_pop*125*nz*ny*nx doubles. */
+sllbm_status sllbm3d_get_state(sllbm3d_ctx* ctx, double* dst_dev);
+sllbm_status sllbm3d_set_state(sllbm3d_ctx* ctx, const double* src_dev);
+const char* sllbm3d_last_error(const sllbm3d_ctx* ctx);
 
 /* Name of the kernel the step uses for this context ("uniform_fused", "gather", "plain_f64"). */
 const char* sllbm_step_kernel_name(const sllbm_ctx* ctx);

@@ -19,7 +19,7 @@ BC_PERIODIC, BC_ZERO_GRADIENT = 0, 1
 NODES_GLC, NODES_EQUIDISTANT = 0, 1
 MAP_IDENTITY, MAP_SINE = 0, 1
 PREC_F32, PREC_BF16_STORE, PREC_F64_PLAIN = 0, 1, 2
-VEL_D2Q25, VEL_D2Q9 = 0, 1
+VEL_D2Q25, VEL_D2Q9, VEL_D3Q125 = 0, 1, 2
 VELSETS = {"d2q25": VEL_D2Q25, "d2q9": VEL_D2Q9}
 PRECISIONS = {"f32": PREC_F32, "bf16": PREC_BF16_STORE, "f64": PREC_F64_PLAIN}
 
@@ -30,6 +30,9 @@ EXPORTS = [
     "sllbm_init_equilibrium", "sllbm_step", "sllbm_step_host", "sllbm_moments", "sllbm_get_state",
     "sllbm_set_state", "sllbm_adjoint_step", "sllbm_init_equilibrium_vjp", "sllbm_step_kernel_name",
     "sllbm_launches_per_step", "sllbm_status_string", "sllbm_last_error", "sllbm_moments_noalloc",
+    "sllbm3d_create", "sllbm3d_destroy", "sllbm3d_grid_info", "sllbm3d_vertex_coords",
+    "sllbm3d_precompute_departures", "sllbm3d_init_equilibrium", "sllbm3d_step", "sllbm3d_moments",
+    "sllbm3d_get_state", "sllbm3d_set_state", "sllbm3d_last_error",
 ]
 
 
@@ -38,6 +41,14 @@ class GridDesc(ctypes.Structure):
                 ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double),
                 ("y1", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
                 ("nodes", ctypes.c_int), ("map", ctypes.c_int), ("map_param", ctypes.c_double * 4)]
+
+
+class GridDesc3(ctypes.Structure):
+    _fields_ = [("nx_cells", ctypes.c_int), ("ny_cells", ctypes.c_int), ("nz_cells", ctypes.c_int),
+                ("order", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("z0", ctypes.c_double),
+                ("z1", ctypes.c_double), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int),
+                ("bc_z", ctypes.c_int), ("nodes", ctypes.c_int)]
 
 
 class Params(ctypes.Structure):
@@ -88,6 +99,17 @@ def load(path: str | None = None):
         "sllbm_status_string": ([I], ctypes.c_char_p),
         "sllbm_moments_noalloc": ([V, I, I, D, V, V, V, V, V, V, P], I),
         "sllbm_last_error": ([P], ctypes.c_char_p),
+        "sllbm3d_create": ([ctypes.POINTER(GridDesc3), ctypes.POINTER(Params), P, ctypes.POINTER(P)], I),
+        "sllbm3d_destroy": ([P], I),
+        "sllbm3d_grid_info": ([P] + [ctypes.POINTER(I)] * 4, I),
+        "sllbm3d_vertex_coords": ([P, V, V, V], I),
+        "sllbm3d_precompute_departures": ([P], I),
+        "sllbm3d_init_equilibrium": ([P, V, V, V, V, V], I),
+        "sllbm3d_step": ([P, I], I),
+        "sllbm3d_moments": ([P, V, V, V, V, V], I),
+        "sllbm3d_get_state": ([P, V], I),
+        "sllbm3d_set_state": ([P, V], I),
+        "sllbm3d_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -255,3 +277,82 @@ class SLLBM:
         self._check(self.lib.sllbm_init_equilibrium_vjp(self.h, *[_ptr(t) for t in ts], _ptr(lam0),
                                                         _ptr(du), _ptr(dv)))
         return du, dv
+
+
+class SLLBM3D:
+    """The 3D extension (D3Q125, hexahedral cells, plain FP64 step) on the current CUDA device."""
+
+    def __init__(self, *, cells, order, box, bc, dt, tau, cv, isothermal=False,
+                 nodes=NODES_GLC, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("SLLBM3D needs a CUDA device; there is no CPU path")
+        self.torch = torch
+        self.lib = load()
+        (x0, x1), (y0, y1), (z0, z1) = box
+        g = GridDesc3(*cells, order, x0, x1, y0, y1, z0, z1, *bc, nodes)
+        p = Params(VEL_D3Q125, dt, tau, cv, 1.0, PREC_F64_PLAIN, 1.0, int(bool(isothermal)))
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self.lib.sllbm3d_create(ctypes.byref(g), ctypes.byref(p),
+                                     ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise SLLBMError(st, self.lib.sllbm_status_string(st).decode())
+        self.h = h
+        n = [ctypes.c_int() for _ in range(4)]
+        self._check(self.lib.sllbm3d_grid_info(h, *[ctypes.byref(x) for x in n]))
+        self.nx, self.ny, self.nz, self.npop = (x.value for x in n)
+        self.shape = (self.nz, self.ny, self.nx)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def _check(self, status):
+        if status != OK:
+            raise SLLBMError(status, self.lib.sllbm3d_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sllbm3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _field(self):
+        return self.torch.empty(self.shape, dtype=self.torch.float64, device=self.device)
+
+    def coords(self):
+        x, y, z = self._field(), self._field(), self._field()
+        self._check(self.lib.sllbm3d_vertex_coords(self.h, _ptr(x), _ptr(y), _ptr(z)))
+        return x, y, z
+
+    def precompute(self):
+        self._check(self.lib.sllbm3d_precompute_departures(self.h))
+
+    def init(self, rho, u, v, w, T):
+        ts = [self.torch.as_tensor(a, dtype=self.torch.float64, device=self.device).contiguous()
+              for a in (rho, u, v, w, T)]
+        for t in ts:
+            assert t.numel() == self.nx * self.ny * self.nz
+        self._check(self.lib.sllbm3d_init_equilibrium(self.h, *[_ptr(t) for t in ts]))
+        self._init_inputs = ts
+
+    def step(self, n=1):
+        self._check(self.lib.sllbm3d_step(self.h, int(n)))
+
+    def moments(self):
+        out = {k: self._field() for k in ("rho", "u", "v", "w", "T")}
+        self._check(self.lib.sllbm3d_moments(self.h, *[_ptr(out[k]) for k in ("rho", "u", "v", "w", "T")]))
+        return out
+
+    def get_state(self):
+        out = self.torch.empty((self.npop, 125) + self.shape, dtype=self.torch.float64, device=self.device)
+        self._check(self.lib.sllbm3d_get_state(self.h, _ptr(out)))
+        return out
+
+    def set_state(self, t):
+        t = t.contiguous()
+        assert t.dtype == self.torch.float64 and t.numel() == self.npop * 125 * self.nx * self.ny * self.nz
+        self._check(self.lib.sllbm3d_set_state(self.h, _ptr(t)))

@@ -12,7 +12,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sllbm_[a-z0-9_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(sllbm(?:3d)?_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declarations_are_bound():
@@ -72,6 +72,21 @@ def test_host_validation_of_sizes_and_options():
         p = ok_params()
         setattr(p, field, value)
         assert create(ok_grid(), p) == status, (field, value)
+    # the 3D entry point: its own velocity set and FP64 only, checked before any CUDA call
+    h3 = ctypes.c_void_p()
+    g3 = sllbm.GridDesc3(2, 2, 2, 2, 0.0, 1.0, 0.0, 1.0, 0.0, 1.0, 0, 0, 0, 0)
+    p3 = lambda **kw: sllbm.Params(kw.get("velset", sllbm.VEL_D3Q125), 0.01, 0.8, kw.get("cv", 2.5), 1.0,
+                                   kw.get("prec", sllbm.PREC_F64_PLAIN), kw.get("pr", 1.0),
+                                   kw.get("iso", 0))
+    create3 = lambda g, p: lib.sllbm3d_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h3))
+    assert create3(g3, p3(velset=0)) == sllbm.ERR_UNSUPPORTED
+    assert create3(g3, p3(prec=sllbm.PREC_F32)) == sllbm.ERR_UNSUPPORTED
+    assert create3(g3, p3(pr=0.75)) == sllbm.ERR_UNSUPPORTED
+    assert create3(g3, p3(iso=1)) == sllbm.ERR_ARG                 # isothermal needs cv = 3/2
+    assert create3(g3, p3(cv=1.0)) == sllbm.ERR_ARG
+    g3.nz_cells = 0
+    assert create3(g3, p3()) == sllbm.ERR_ARG
+    assert create(ok_grid(), p3()) == sllbm.ERR_UNSUPPORTED         # the 2D context refuses D3Q125
     # D2Q9 with the isothermal configuration but a Prandtl number other than 1
     p = sllbm.Params(sllbm.VEL_D2Q9, 0.01, 0.8, 1.0, 1.0, 0, 0.75, 1)
     assert create(ok_grid(), p) == sllbm.ERR_UNSUPPORTED
