@@ -19,8 +19,9 @@ import math
 
 import numpy as np
 import pytest
-import sympy as sp
 from scipy.interpolate import BarycentricInterpolator
+
+sp = pytest.importorskip("sympy")   # not every test machine has it
 
 from oracle import sllbm as o
 
