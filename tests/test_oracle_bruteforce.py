@@ -28,11 +28,12 @@ from oracle import sllbm as o
 CV = 2.5
 
 
-def _velocity_set():
-    nodes, weights = np.polynomial.hermite_e.hermegauss(5)
+def _velocity_set(n1=5):
+    """1D rule in the oracle's order: D1Q5 as in Table I (0, +small, +large, -small, -large),
+    D1Q3 as 0, +sqrt3, -sqrt3."""
+    nodes, weights = np.polynomial.hermite_e.hermegauss(n1)
     weights = weights / math.sqrt(2 * math.pi)
-    # Table I order: 0, +small, +large, -small, -large
-    order = [2, 3, 4, 1, 0]
+    order = [2, 3, 4, 1, 0] if n1 == 5 else [1, 2, 0]
     return nodes[order], weights[order]
 
 
@@ -57,6 +58,7 @@ GH_W = GH_W / math.sqrt(2 * math.pi)
 
 
 def _feq(rho, ux, uy, theta, xi1, w1):
+    n1 = len(xi1)
     sd = math.sqrt(theta)
     coef = {}
     for (n, idx), h in H.items():
@@ -65,18 +67,19 @@ def _feq(rho, ux, uy, theta, xi1, w1):
             for zb, wb in zip(GH_Z, GH_W):
                 s += wa * wb * h(ux + sd * za, uy + sd * zb)
         coef[n, idx] = rho * s
-    f = np.zeros(25)
-    for a in range(5):
-        for b in range(5):
+    f = np.zeros(n1 * n1)
+    for a in range(n1):
+        for b in range(n1):
             acc = 0.0
             for (n, idx), h in H.items():
                 acc += coef[n, idx] * h(xi1[a], xi1[b]) / math.factorial(n)
-            f[5 * a + b] = w1[a] * w1[b] * acc
+            f[n1 * a + b] = w1[a] * w1[b] * acc
     return f
 
 
-def _step(F, G, nodes, n_cells, lengths, dt, tau, xi1, w1):
-    """One step on a periodic grid: F, G are [25][ny][nx] post-collision fields."""
+def _step(F, G, nodes, n_cells, lengths, dt, tau, xi1, w1, cv=CV, isothermal=False):
+    """One step on a periodic grid: F, G are [q][ny][nx] post-collision fields."""
+    n1 = len(xi1)
     ny, nx = F.shape[1:]
     p = len(nodes) - 1
     (Lx, Ly), (cx, cy) = lengths, n_cells
@@ -84,31 +87,31 @@ def _step(F, G, nodes, n_cells, lengths, dt, tau, xi1, w1):
     xs = [hx * (j // p + nodes[j % p]) for j in range(nx)]
     ys = [hy * (j // p + nodes[j % p]) for j in range(ny)]
     Fn, Gn = np.zeros_like(F), np.zeros_like(G)
-    K = 2 * CV - 2
+    K = 2 * cv - 2
+    vel = [(a, b) for a in range(n1) for b in range(n1)]
     for iy in range(ny):
         for ix in range(nx):
-            fpre, gpre = np.zeros(25), np.zeros(25)
-            for a in range(5):
-                for b in range(5):
-                    i = 5 * a + b
-                    xd = (xs[ix] - dt * xi1[a]) % Lx
-                    yd = (ys[iy] - dt * xi1[b]) % Ly
-                    kx, ky = min(int(xd // hx), cx - 1), min(int(yd // hy), cy - 1)
-                    rx, ry = xd / hx - kx, yd / hy - ky
-                    for src, dst in ((F, fpre), (G, gpre)):
-                        rows = []
-                        for m in range(p + 1):
-                            jy = (ky * p + m) % ny
-                            vals = [src[i, jy, (kx * p + q) % nx] for q in range(p + 1)]
-                            rows.append(float(BarycentricInterpolator(nodes, vals)(rx)))
-                        dst[i] = float(BarycentricInterpolator(nodes, rows)(ry))
+            fpre, gpre = np.zeros(n1 * n1), np.zeros(n1 * n1)
+            for a, b in vel:
+                i = n1 * a + b
+                xd = (xs[ix] - dt * xi1[a]) % Lx
+                yd = (ys[iy] - dt * xi1[b]) % Ly
+                kx, ky = min(int(xd // hx), cx - 1), min(int(yd // hy), cy - 1)
+                rx, ry = xd / hx - kx, yd / hy - ky
+                for src, dst in ((F, fpre), (G, gpre)):
+                    rows = []
+                    for m in range(p + 1):
+                        jy = (ky * p + m) % ny
+                        vals = [src[i, jy, (kx * p + q) % nx] for q in range(p + 1)]
+                        rows.append(float(BarycentricInterpolator(nodes, vals)(rx)))
+                    dst[i] = float(BarycentricInterpolator(nodes, rows)(ry))
             rho = fpre.sum()
-            jx = sum(fpre[5 * a + b] * xi1[a] for a in range(5) for b in range(5))
-            jy = sum(fpre[5 * a + b] * xi1[b] for a in range(5) for b in range(5))
-            e2 = sum(fpre[5 * a + b] * (xi1[a] ** 2 + xi1[b] ** 2) for a in range(5) for b in range(5))
+            jx = sum(fpre[n1 * a + b] * xi1[a] for a, b in vel)
+            jy = sum(fpre[n1 * a + b] * xi1[b] for a, b in vel)
+            e2 = sum(fpre[n1 * a + b] * (xi1[a] ** 2 + xi1[b] ** 2) for a, b in vel)
             e2 += gpre.sum()
             ux, uy = jx / rho, jy / rho
-            theta = (e2 - rho * (ux * ux + uy * uy)) / (2 * CV * rho)
+            theta = 1.0 if isothermal else (e2 - rho * (ux * ux + uy * uy)) / (2 * cv * rho)
             feq = _feq(rho, ux, uy, theta, xi1, w1)
             Fn[:, iy, ix] = fpre - (fpre - feq) / tau
             Gn[:, iy, ix] = gpre - (gpre - K * theta * feq) / tau
@@ -140,3 +143,22 @@ def test_one_step_matches_an_independent_transcription(p, cells):
     scale = np.max(np.abs(f1))
     assert np.max(np.abs(f1 - F2)) < 1e-12 * scale
     assert np.max(np.abs(g1 - G2)) < 1e-12 * scale
+
+
+def test_d2q9_isothermal_step_matches_an_independent_transcription():
+    """The same on the D2Q9 set (numpy's three-point rule) with the isothermal equilibrium."""
+    p, cells, Lx, Ly = 2, (2, 2), 1.0, 0.8
+    rng = np.random.default_rng(77)
+    grid = o.Grid(o.Axis(cells[0], p, 0.0, Lx, True), o.Axis(cells[1], p, 0.0, Ly, True))
+    X, Y = grid.coords()
+    rho = 1 + 0.05 * rng.standard_normal(X.shape)
+    u = 0.08 * rng.standard_normal(X.shape)
+    v = 0.08 * rng.standard_normal(X.shape)
+    f, g = o.initial_state(rho, u, v, np.ones_like(X), 1.0, q=9)
+    f = f * (1 + 0.02 * rng.standard_normal(f.shape))
+    dt, tau = 0.031, 0.9
+    f1, g1 = o.step(f, g, o.Departures(grid, dt, q=9), tau, 1.0, isothermal=True)
+    xi1, w1 = _velocity_set(3)
+    nodes = 0.5 * (1 + np.polynomial.chebyshev.chebpts2(p + 1))
+    F2, _ = _step(f, g, nodes, cells, (Lx, Ly), dt, tau, xi1, w1, cv=1.0, isothermal=True)
+    assert np.max(np.abs(f1 - F2)) < 1e-12 * np.max(np.abs(f1))
