@@ -192,13 +192,16 @@ sllbm_status sllbm_init_equilibrium_vjp(sllbm_ctx* ctx, const double* rho_dev, c
  *              with n_pop = 1 if cv == 1, else 2 (caller-owned, device);
  *   A_dev:     vertex weights (sllbm_vertex_weights, nx*ny doubles) or NULL to skip the sums;
  *   rho/u/v/T: FP32 outputs of nx*ny floats, each may be NULL;
- *   mass_energy_dev: two doubles on the device, written only if A_dev is given.
+ *   mass_energy_dev: two doubles on the device, written only if A_dev is given (required then,
+ *              may be NULL otherwise).
  * Its reduction scratch is a file-scope device array of 1 MiB (the library keeps it on every GPU
  * that loads it until the process exits), so grids are limited to 16,777,216 vertices
- * (SLLBM_ERR_UNSUPPORTED beyond).  The first call on a device looks up that array's address;
- * make that first call before any stream capture.  All calls share the array: calls that
- * overlap on the GPU (other streams, other threads) race; serialise them.  Synchronises
- * cuda_stream; returns SLLBM_ERR_UNSTABLE like sllbm_moments. */
+ * (SLLBM_ERR_UNSUPPORTED beyond, checked before anything is launched).  Every call looks up that
+ * array's device address on the current device (a host-side query, nothing cached), so a call
+ * made after the device's context was rebuilt finds the array where it now is.  The first call
+ * in a process may load the library's device code; make it before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU (other streams, other threads) race;
+ * serialise them.  Synchronises cuda_stream; returns SLLBM_ERR_UNSTABLE like sllbm_moments. */
 sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, int ny, double cv,
                                    const double* A_dev, float* rho_dev, float* u_dev, float* v_dev,
                                    float* T_dev, double* mass_energy_dev, void* cuda_stream);

@@ -120,7 +120,9 @@ cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s) {
 // The reduction needs per-block FP64 partials and an instability flag.  Here they live in a
 // file-scope device array instead of memory the caller or a context allocates.  Every GPU that
 // loads the library holds this array until the process exits.  In host code the symbol is only
-// a stand-in, so its device address is looked up once per device with cudaGetSymbolAddress.
+// a stand-in, so its device address is looked up with cudaGetSymbolAddress on every call, with
+// the caller's device current: a host-side query that enqueues nothing, so no address is cached
+// that a rebuilt context could invalidate and concurrent first calls share no host state.
 // ------------------------------------------------------------------------------------------
 #include <math.h>
 
@@ -129,24 +131,15 @@ cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s) {
 namespace sllbm {
 
 constexpr int kNoAllocMaxBlocks = 65536;   // => at most 65536 * 256 = 16,777,216 vertices
+constexpr long long kNoAllocMaxVertices = (long long)kNoAllocMaxBlocks * kMomThreads;
 // layout: [0, 2 * kNoAllocMaxBlocks) doubles of partials, then one int flag (in a double slot)
 static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocMaxBlocks + 2];
 
-constexpr int kMaxDevices = 64;
-static double* g_noalloc_ptr[kMaxDevices];   // device address of the array, per device
-
 static cudaError_t noalloc_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -157,9 +150,10 @@ extern "C" sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, in
                                               float* v_dev, float* T_dev, double* mass_energy_dev,
                                               void* cuda_stream) {
   using namespace sllbm;
-  if (!state_dev || !mass_energy_dev || nx < 1 || ny < 1 || !(cv >= 1.0)) return SLLBM_ERR_ARG;
+  if (!state_dev || nx < 1 || ny < 1 || !(cv >= 1.0)) return SLLBM_ERR_ARG;
+  if (A_dev && !mass_energy_dev) return SLLBM_ERR_ARG;   // the sums need somewhere to go
   const long long nv = (long long)nx * ny;
-  if (moments_blocks(nv) > kNoAllocMaxBlocks) return SLLBM_ERR_UNSUPPORTED;   // > 16,777,216 vertices
+  if (nv > kNoAllocMaxVertices) return SLLBM_ERR_UNSUPPORTED;   // checked before any int cast
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double* scratch = nullptr;
   if (noalloc_scratch(&scratch) != cudaSuccess) return SLLBM_ERR_CUDA;
@@ -187,7 +181,7 @@ extern "C" sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, in
   a.v = v_dev;
   a.T = T_dev;
   a.partials = A_dev ? scratch : nullptr;   // the block partials are all overwritten: no clearing
-  a.sums = mass_energy_dev;
+  a.sums = A_dev ? mass_energy_dev : nullptr;
   a.flag = flag;
   if (launch_moments(a, s) != cudaSuccess) return SLLBM_ERR_CUDA;
   int host_flag = 0;
