@@ -151,6 +151,8 @@ static void build_consts(Consts& cs, int velset) {
     cs.wf[a] = (float)w[a];
     for (int k = 0; k < 5; ++k) cs.hef[k][a] = (float)cs.he[k][a];
   }
+  cs.inv_xi1f = (float)(1.0 / xi[1]);
+  cs.xi1sqf = (float)(xi[1] * xi[1]);
 }
 
 static void build_axis(AxisK& ax, int n_cells, int p, double lo, double hi, int periodic, int nodes) {

@@ -26,6 +26,7 @@ struct Consts {
   double he[kQ1][kQ1];
   float xif[kQ1], wf[kQ1], hef[kQ1][kQ1];
   int nq1;   // 1D nodes of the set: 5 (D2Q25) or 3 (D2Q9); velocity i = nq1 a + b
+  float inv_xi1f, xi1sqf;   // 1 / xi_1 and xi_1^2 (xi_1 the first nonzero node), FP32
 };
 
 // One axis of the grid as the kernels see it (Sec. II.E): n_cells cells of order p on [lo, hi].
@@ -267,7 +268,7 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
     for (int a = 0; a < kQ1; ++a) G += rs[a].y;
   }
   const float rho = 1.f + drho;
-  const float inv_rho = 1.f / rho;
+  const float inv_rho = __frcp_rn(rho);
   const float ux = jx * inv_rho, uy = jy * inv_rho;
   // Pr != 1 (Sec. II.C): the non-equilibrium centred third moments of f and g, as (f, g) pairs
   // xxx, xxy, xyy, yyy.  The equilibrium's centred third moment is zero, so they are those of the
@@ -380,9 +381,8 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
     relax(3, b, ev[1] - od[1], t[1]);
     relax(4, b, ev[2] - od[2], t[2]);
   }
-  // Residual moments of (equilibrium - pre-collision state); remove them with the smallest
-  // correction in the span of w {1, xi_x, xi_y} (mass, momentum) and w on g (energy).  This
-  // changes nothing in exact arithmetic and restores conservation to the rounding of the sums.
+  // Residual moments of (equilibrium - pre-collision state): mass, x and y momentum of f, and
+  // the energy of f and g.
   float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, rg = 0.f;
 #pragma unroll
   for (int a = 0; a < kQ1; ++a) {
@@ -393,29 +393,28 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
     rg += drow[a].y;
   }
   if (cp.npop == 2) r3 += rg;
-  const float c3 = r3 - 2.f * r0;   // energy residual left after the mass correction
-  // per b: w_b r2 xi_b and w_b c3, so that each velocity takes three FMAs (the g term is shared
-  // by a component and its mirror)
-  float r2w[kQ1], c3w[kQ1];
-#pragma unroll
-  for (int b = 0; b < kQ1; ++b) {
-    r2w[b] = r2 * (cs.wf[b] * cs.xif[b]);
-    c3w[b] = c3 * cs.wf[b];
-  }
-#pragma unroll
-  for (int a = 0; a <= 2; ++a) {
-    const float ta = om * cs.wf[a];
-    const float ca = r0 + r1 * cs.xif[a], cm = r0 - r1 * cs.xif[a];
-#pragma unroll
-    for (int b = 0; b < kQ1; ++b) {
-      // om w_a w_b (r0 + r1 xi_a + r2 xi_b) on f, om w_a w_b c3 on g
-      const float tg = ta * c3w[b];
-      fg[5 * a + b].x -= ta * (ca * cs.wf[b] + r2w[b]);
-      fg[5 * a + b].y -= tg;
-      if (a > 0) {
-        fg[5 * (a + 2) + b].x -= ta * (cm * cs.wf[b] + r2w[b]);
-        fg[5 * (a + 2) + b].y -= tg;
-      }
+  // Remove the residuals at the fewest velocities that span the conserved moments: mass and
+  // momentum on f at the rest velocity and at the two velocities with one small component,
+  // xi = (s, 0) (i = 5) and (0, s) (i = 1); the energy left after that on g at the rest velocity
+  // (g carries energy only).  This changes nothing in exact arithmetic and restores conservation
+  // to the rounding of the sums.
+  {
+    const float inv_s = cs.inv_xi1f, s2 = cs.xi1sqf;
+    const float d1 = r1 * inv_s, d2 = r2 * inv_s;
+    const float d0 = r0 - d1 - d2;
+    const float de = r3 - s2 * (d1 + d2);   // energy residual left after the mass/momentum fix
+    fg[0].x -= om * d0;
+    fg[5].x -= om * d1;
+    fg[1].x -= om * d2;
+    if (cp.npop == 2) {
+      fg[0].y -= om * de;
+    } else if (!cp.iso) {
+      // one population: along (xi = (+-s, 0): +e, rest: -2e), which carries no mass or
+      // momentum and the energy 2 s^2 e
+      const float e = om * 0.5f * de * inv_s * inv_s;
+      fg[5].x -= e;
+      fg[15].x -= e;
+      fg[0].x += 2.f * e;
     }
   }
   if constexpr (PR) {
@@ -445,18 +444,6 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
         fg[5 * a + b] = fma2(bcast2(wh3[b]), B3, t);
       }
     }
-  }
-  if (cp.npop != 2 && !cp.iso) {
-    // single population: remove the energy residual along w (|xi|^2 - 2), which carries no
-    // mass or momentum; its energy is sum w |xi|^4 - 2 sum w |xi|^2 = 8 - 4 = 4
-    const float c = 0.25f * c3;
-#pragma unroll
-    for (int a = 0; a < kQ1; ++a)
-#pragma unroll
-      for (int b = 0; b < kQ1; ++b) {
-        const float x2 = cs.xif[a] * cs.xif[a] + cs.xif[b] * cs.xif[b];
-        fg[5 * a + b].x -= om * cs.wf[a] * cs.wf[b] * c * (x2 - 2.f);
-      }
   }
   return (rho > 0.f) && (q > -1.f) && isfinite(rho) && isfinite(q);
 }

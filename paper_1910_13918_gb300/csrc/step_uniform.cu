@@ -65,11 +65,14 @@ struct TileShape {
 constexpr int kStageBuffers = 4;   // TMA staging buffers per CTA (prefetch distance 3 stages)
 constexpr int kCO = 4;             // staged column origin x0 - 4: 16-byte aligned for both pair types
 constexpr int kC = 32 + 2 * kCO;   // staged columns
-// Rows of the y-pass output T keep column c at c + c / 16: a gap every 16 columns spreads the
-// cell-aligned reads of the x pass (lanes of one cell read the same columns, cells 4 columns
-// apart) over all shared-memory banks.
-constexpr int kTC = kC + kC / 16;  // T row length (pairs)
-__host__ __device__ constexpr int tpos(int c) { return c + (c >> 4); }
+// Rows of the y-pass output T keep column c at a skewed position: the lanes of one cell read the
+// same columns and cells are P columns apart, so plain rows would put several cells on one
+// shared-memory bank.  With a gap every 16 columns (P = 4, 2, 1) or two every 17 (P = 3) the
+// x-pass reads of each tap and the y-pass row stores are free of bank conflicts.
+template <int P>
+__host__ __device__ constexpr int tpos(int c) { return P == 3 ? c + 2 * (c / 17) : c + (c >> 4); }
+template <int P>
+struct TRow { static constexpr int N = tpos<P>(kC - 1) + 1; };   // T row length (pairs)
 // ints of the DX [5][P] and EY [5] tables, rounded up to keep the mbarriers 8-byte aligned
 __host__ __device__ constexpr int table_ints(int P) { return (kQ1 * P + kQ1 + 1) / 2 * 2; }
 
@@ -80,6 +83,20 @@ struct BoxShape {
   static constexpr int BYTES = ELEMS * (int)sizeof(Store);
   static constexpr int STRIDE = ((BYTES + 127) / 128) * 128 / (int)sizeof(Store);
 };
+
+// The P tail-sum taps of one (component, local node), stored as 4 (f, g) pairs (32 bytes,
+// 16-byte aligned): two 16-byte loads.
+template <int P>
+__device__ __forceinline__ void load_taps(const float2* w, float2 (&W)[P]) {
+  const float4 q0 = *reinterpret_cast<const float4*>(w);
+  W[0] = make_float2(q0.x, q0.y);
+  if (P > 1) W[1] = make_float2(q0.z, q0.w);
+  if (P > 2) {
+    const float4 q1 = *reinterpret_cast<const float4*>(w + 2);
+    W[2 < P ? 2 : 0] = make_float2(q1.x, q1.y);
+    if (P > 3) W[3 < P ? 3 : 0] = make_float2(q1.z, q1.w);
+  }
+}
 
 // y interpolation of the RC rows of a task.  Window row j is task row j - P; row rr = m p + l
 // has its stencil in cell m + e of the window (rows (m + e) p .. (m + e + 1) p), e = 1 except
@@ -95,7 +112,7 @@ __device__ __forceinline__ void y_rows(const float2 (&win)[RW], const float2 (&d
     float2 acc = win[s];
 #pragma unroll
     for (int al = 1; al <= P; ++al) acc = fma2(W[l][al - 1], dl[s + al - 1], acc);
-    tout[rr * kTC] = acc;
+    tout[rr * TRow<P>::N] = acc;
   }
 }
 
@@ -108,7 +125,10 @@ __device__ __forceinline__ void y_pass(const Store* __restrict__ Sst, float2* __
                                     const float2* __restrict__ WY, const int* __restrict__ EY) {
   using TS = TileShape<P, Tall>;
   constexpr int TY = TS::TY, R = TS::R, NH = TS::NH, RC = TS::RC, RW = TS::RW, NT = TS::NT;
-  constexpr int CR = kC - 32;
+  // The x pass reads staged columns [4 - P, 36 + P) only (stencil starts in [-P, 0] from the
+  // column, P + 1 taps): 32 columns per plane in the warp tasks, the 2P others in the packed ones.
+  constexpr int C0 = kCO - P;
+  constexpr int CR = 2 * P;
   static_assert(NH * CR <= 32, "right-hand columns of one plane must fit in a warp");
   // right-hand columns: one warp per plane b if the block has the warps, else packed
   constexpr bool kSpread = kQ1 * (NH + 1) * 32 <= NT;
@@ -121,19 +141,19 @@ __device__ __forceinline__ void y_pass(const Store* __restrict__ Sst, float2* __
       const int g = t >> 5;
       b = g / NH;
       h = g - b * NH;
-      c = t & 31;
+      c = C0 + (t & 31);
     } else if (kSpread) {
       const int u = t - kQ1 * NH * 32, lane = u & 31;
       if (lane >= NH * CR) continue;
       b = u >> 5;
       h = lane / CR;
-      c = 32 + lane - h * CR;
+      c = C0 + 32 + lane - h * CR;
     } else {
       const int u = t - kQ1 * NH * 32;
       b = u / (NH * CR);
       const int r = u - b * NH * CR;
       h = r / CR;
-      c = 32 + r - h * CR;
+      c = C0 + 32 + r - h * CR;
     }
     const Store* col = Sst + ((size_t)(b * R + h * RC) * kC + c) * 2;
     float2 win[RW], dl[RW - 1];
@@ -141,12 +161,10 @@ __device__ __forceinline__ void y_pass(const Store* __restrict__ Sst, float2* __
     for (int j = 0; j < RW; ++j) win[j] = lds_pair(col + j * kC * 2);
 #pragma unroll
     for (int j = 0; j < RW - 1; ++j) dl[j] = sub2(win[j + 1], win[j]);
-    float2* tout = Tst + ((size_t)b * TY + h * RC) * kTC + tpos(c);
+    float2* tout = Tst + ((size_t)b * TY + h * RC) * TRow<P>::N + tpos<P>(c);
     float2 W[P][P];   // tail sums of the plane's P row classes, in registers
 #pragma unroll
-    for (int l = 0; l < P; ++l)
-#pragma unroll
-      for (int al = 0; al < P; ++al) W[l][al] = WY[(b * P + l) * 4 + al];
+    for (int l = 0; l < P; ++l) load_taps<P>(WY + (b * P + l) * 4, W[l]);
     if (EY[b])
       y_rows<P, RC, RW, true>(win, dl, W, tout);
     else
@@ -186,8 +204,8 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   extern __shared__ unsigned char smem_dyn[];
   unsigned char* smem_raw = smem_dyn + ((128 - (smem_u32(smem_dyn) & 127)) & 127);
   Store* S = reinterpret_cast<Store*>(smem_raw);                        // [NSB][box]
-  float2* T = reinterpret_cast<float2*>(S + NSB * BS::STRIDE);         // [2][5][TY][kTC]
-  float2* WX = T + 2 * kQ1 * TY * kTC;                                 // [5][P][4]: (W, W)
+  float2* T = reinterpret_cast<float2*>(S + NSB * BS::STRIDE);         // [2][5][TY][TRow]
+  float2* WX = T + 2 * kQ1 * TY * TRow<P>::N;                                 // [5][P][4]: (W, W)
   float2* WY = WX + kQ1 * P * 4;                                       // [5][P][4]
   int* DX = reinterpret_cast<int*>(WY + kQ1 * P * 4);                  // [5][P]
   int* EY = DX + kQ1 * P;                                              // [5]
@@ -215,7 +233,7 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   // Global stage counter: the k-th tile of this CTA has stages 5k .. 5k+4; stage s lands in
   // S[s % NSB] and completes phase (s / NSB) & 1 of BAR[s % NSB]; it is issued PD stages ahead, so
   // the first stages of the next tile are in flight while a tile finishes and collides.
-  auto issue = [&](int tile, int st, long s) {
+  auto issue = [&](int tile, int st, int s) {
     if (tid == 0 && tile < ntiles) {
       const int buf = (int)(s % NSB);
       const int tx0 = (tile % tiles_x) * 32, ty0 = (tile / tiles_x) * TY;
@@ -242,7 +260,7 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
 #pragma unroll
     for (int j = 0; j < kQ1; ++j) {
       if (!ycur && j > 0) break;   // after the last tile: its x pass of stage 4 and collision
-      const long s = (long)kQ1 * k + j;
+      const int s = kQ1 * k + j;
       if (ycur) mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);  // stage landed
       __syncthreads();  // T[(s-1)&1] written; T[s&1] and S[(s+PD)%NSB] no longer read
       if (ycur) {
@@ -250,7 +268,7 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
           issue(tile, j + PD, s + PD);
         else
           issue(tile + gridDim.x, j + PD - kQ1, s + PD);   // the next tile's first stages
-        y_pass<P, Tall, Store>(S + (size_t)(s % NSB) * BS::STRIDE, T + (size_t)(s & 1) * kQ1 * TY * kTC,
+        y_pass<P, Tall, Store>(S + (size_t)(s % NSB) * BS::STRIDE, T + (size_t)(s & 1) * kQ1 * TY * TRow<P>::N,
                                WY, EY);
       }
       if (k == 0 && j == 0) continue;   // no stage before the first
@@ -265,22 +283,20 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
         const int kx = x % P;
         const float2* w = WX + (st * P + kx) * 4;
         const int cbase = lane + kCO + DX[st * P + kx];
-        float2 W[P + 1];
+        float2 W[P];
+        load_taps<P>(w, W);
         int tp[P + 1];   // T positions of the stencil columns
 #pragma unroll
-        for (int al = 0; al <= P; ++al) {
-          if (al) W[al] = w[al - 1];
-          tp[al] = tpos(cbase + al);
-        }
-        const float2* trow0 = T + ((size_t)((s - 1) & 1) * kQ1 * TY + row) * kTC;
+        for (int al = 0; al <= P; ++al) tp[al] = tpos<P>(cbase + al);
+        const float2* trow0 = T + ((size_t)((s - 1) & 1) * kQ1 * TY + row) * TRow<P>::N;
 #pragma unroll
         for (int b = 0; b < kQ1; ++b) {
-          const float2* trow = trow0 + b * TY * kTC;
+          const float2* trow = trow0 + b * TY * TRow<P>::N;
           float2 prev = trow[tp[0]], acc = prev;
 #pragma unroll
           for (int al = 1; al <= P; ++al) {
             const float2 cur = trow[tp[al]];
-            acc = fma2(W[al], sub2(cur, prev), acc);
+            acc = fma2(W[al - 1], sub2(cur, prev), acc);
             prev = cur;
           }
           fg[5 * st + b] = acc;
@@ -314,7 +330,7 @@ template <int P, typename Store, bool Tall>
 static size_t smem_bytes() {
   using TS = TileShape<P, Tall>;
   using BS = BoxShape<P, Tall, Store>;
-  return 128 + sizeof(Store) * kStageBuffers * BS::STRIDE + sizeof(float2) * 2 * kQ1 * TS::TY * kTC +
+  return 128 + sizeof(Store) * kStageBuffers * BS::STRIDE + sizeof(float2) * 2 * kQ1 * TS::TY * TRow<P>::N +
          sizeof(float2) * 2 * kQ1 * P * 4 + sizeof(int) * table_ints(P) + sizeof(uint64_t) * kStageBuffers;
 }
 

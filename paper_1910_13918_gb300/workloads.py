@@ -331,6 +331,19 @@ def riemann_paper():
     return w
 
 
+def riemann_nodes(nodes="glc", cells=128):
+    """The 2D Riemann run of Sec. III.D as printed: 128 x 128 cells of order p = 4 on [0,1]^2
+    (513 x 513 vertices), the Table III states, tau = 1.94815, t_end = 0.25 after 2091 steps,
+    zero-gradient boundaries; ``nodes`` "glc" or "equidistant" for the comparison of support
+    points (the paper's equidistant run diverged shortly after 200 steps)."""
+    w = Workload(f"riemann{cells}_p4_{nodes}", cells, cells, 4, 0.0, 1.0, 0.0, 1.0, ZERO_GRADIENT,
+                 ZERO_GRADIENT, 0.25 / 2091, 1.94815, 2091, "riemann", nodes=nodes, seed=9,
+                 extra={"states": RIEMANN_STATES_PAPER, "split": 0.5})
+    w.dt *= 128.0 / cells
+    w.steps = int(round(0.25 / w.dt))
+    return w
+
+
 def svi():
     """Shock-vortex interaction on the sine-mapped grid [0,2]x[0,1], 512x256 cells, p = 2.
 
@@ -395,7 +408,8 @@ def sdp(points=16, step_factor=1):
 
 
 ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
-       "riemann_paper": riemann_paper, "svi": svi, "svi_pr": svi_pr, "sdp": sdp,
+       "riemann_paper": riemann_paper, "riemann_glc": riemann_nodes,
+       "riemann_equidistant": lambda: riemann_nodes("equidistant"), "svi": svi, "svi_pr": svi_pr, "sdp": sdp,
        "tgv_moving": tgv_moving,
        # the moving vortex on 2048 x 2048 vertices (state larger than L2), both velocity sets
        "tgvm2048": lambda: tgv_moving(2048, 0.05), "tgvm2048_d2q9": lambda: tgv_moving(2048, 0.05, "d2q9")}

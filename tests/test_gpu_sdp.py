@@ -8,7 +8,11 @@ the smallest GLC spacing), doubled per refinement; nu = 1e-10, so omega = 1/tau 
 Table II's errors drop with about fourth order on coarse grids and second order once the time
 error dominates; here the time error takes over one refinement earlier (from 64 x 64 points) and
 the coarse-grid errors are about 15x smaller than the printed ones, while on the finest grids the
-magnitudes agree within 2x.
+magnitudes agree within 2x.  The 16 x 16 error is a spatial one (the oracle gives 1.41e-3 with
+the printed 1105 steps and 1.44e-3 with twice as many) and no other reading of the units tried
+moves it toward the printed 2.1e-2 (a speed of 0.2 sqrt(gamma): 1.33e-3); so the band below
+only keeps the magnitudes within the spread of those readings, and the FP64 GPU run is pinned
+to the oracle's own run of the whole 16 x 16 case instead.
 """
 import numpy as np
 import pytest
@@ -40,8 +44,8 @@ def test_fp64_errors_and_orders_match_table2(gpu_lib):
         rho, x, y, _ = _run(w, "f64")
         err[n] = H.sdp_error(w, rho, x, y)
     print("smooth density propagation, FP64:", {n: f"{e:.3e}" for n, e in err.items()})
-    for n in sizes:   # never less accurate than printed, and within 30x of it
-        assert t2[n] / 30 < err[n] < 2 * t2[n], (n, err[n], t2[n])
+    for n in sizes:   # never much less accurate than printed, and within 20x of it
+        assert t2[n] / 20 < err[n] < 2 * t2[n], (n, err[n], t2[n])
     order = {n: np.log2(err[n // 2] / err[n]) for n in sizes[1:]}
     assert 3.5 < order[32] < 4.7, order        # spatial order p = 4 on the coarse grids
     assert 1.7 < order[256] < 2.3, order       # second order in time on the fine grids
@@ -83,3 +87,15 @@ def test_sdp_against_oracle(gpu_lib):
             got = tuple(m[k].double().cpu().numpy() for k in ("rho", "u", "v", "T"))
             err = H.field_errors(got, ref, w.velocity_scale)
             assert max(err.values()) < 1e-5, err
+
+
+def test_fp64_16x16_table2_run_equals_the_oracle_run(gpu_lib):
+    """The whole 16 x 16 case (1105 steps to one crossing) on the FP64 GPU step against the
+    oracle's run of it: the same error against the exact solution, and the same density."""
+    w = W.sdp(16)
+    rho, x, y, _ = _run(w, "f64")
+    ref, _, _, _ = H.oracle_run(w, w.steps, perturb=False)
+    X, Y = H.oracle_grid(w).coords()
+    e_gpu, e_ref = H.sdp_error(w, rho, x, y), H.sdp_error(w, ref, X, Y)
+    assert abs(e_gpu - e_ref) <= 1e-9, (e_gpu, e_ref)
+    assert np.max(np.abs(rho - ref.reshape(-1))) <= 1e-10
