@@ -145,6 +145,17 @@ sllbm_status sllbm_init_equilibrium(sllbm_ctx* ctx, const double* rho_dev, const
  * store the post-collision populations.  Enqueues only; returns without synchronising. */
 sllbm_status sllbm_step(sllbm_ctx* ctx, int nsteps);
 
+/* One step as sllbm_step that also writes, per vertex, the moments its collision was evaluated
+ * at: the density, velocity and temperature of the interpolated pre-collision populations (Sec.
+ * II: rho = sum f, rho u = sum f xi, T from 2 rho E = sum f |xi|^2 + sum g; theta = T / T0).
+ * BGK conserves them, so away from FP32 rounding they are the moments sllbm_moments returns for
+ * the state the step produced -- the saved_moments of sllbm_adjoint_step (in the isothermal
+ * configuration, whose collision does not keep the energy, they are the pre-collision ones).
+ * moments_dev: caller-owned device FP32 [4][ny][nx] = (rho, u, v, theta), written by the step
+ * kernels themselves (no second pass over the state).  D2Q25 only (else UNSUPPORTED); enqueues
+ * only. */
+sllbm_status sllbm_step_moments(sllbm_ctx* ctx, float* moments_dev);
+
 /* Same step with host buffers: copies the state (sllbm_state_bytes bytes, dense layout) from
  * state_in_host to the device, advances nsteps, copies it back to state_out_host and
  * synchronises.  Pinned host memory gives the full link bandwidth. */

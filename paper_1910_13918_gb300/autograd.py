@@ -2,9 +2,10 @@
 
 Forward: initial equilibrium of (rho0, u0, v0, T0) (Sec. II.A, II.D), ``nsteps`` fused steps, and
 the final density field.  Backward: the hand-written adjoint of the C library, run in reverse over
-segments of ``k`` steps.  Only every k-th state is kept; each segment is recomputed forward once,
-storing the per-step moments (rho, u, v, theta) the collision Jacobian needs, then the adjoint
-steps walk back through it.  The paper has no adjoint; this is its discrete transpose.
+segments of ``k`` steps.  Only every k-th state is kept; each segment is recomputed forward once
+by steps that also write the per-step moments (rho, u, v, theta) the collision Jacobian needs
+(the step kernels' own epilogue, no separate moments pass), then the adjoint steps walk back
+through it.  The paper has no adjoint; this is its discrete transpose.
 """
 from __future__ import annotations
 
@@ -48,8 +49,7 @@ class SLLBMRollout(torch.autograd.Function):
                 end = min(start + k, nsteps)
                 sim.set_state(checkpoints[start])
                 for j in range(end - start):
-                    sim.step(1)
-                    sim.moments_into(moments[j])          # moments of state start + j + 1
+                    sim.step_moments(moments[j])          # the moments step start + j + 1 used
                 for j in reversed(range(end - start)):
                     sim.adjoint_step(lam, lam_out, moments[j])
                     lam, lam_out = lam_out, lam

@@ -92,14 +92,21 @@ __global__ void __launch_bounds__(128) adjoint_collide_kernel(const __grid_const
   const bool has_g = a.cp.npop == 2;
   EqDerivs<float> d;
   eq_derivs<float>(a.cs.hef, ux, uy, q, d);
+  // the vertex's 50 adjoint values, read once and kept in registers for both passes below
+  float lfv[kQ], lgv[kQ];
+#pragma unroll
+  for (int i = 0; i < kQ; ++i) {
+    lfv[i] = __ldg(a.lam_in + (size_t)i * a.nv + v);
+    lgv[i] = has_g ? __ldg(a.lam_in + (size_t)(kQ + i) * a.nv + v) : 0.f;
+  }
   float yr = 0.f, yux = 0.f, yuy = 0.f, yth = 0.f;
 #pragma unroll
   for (int ia = 0; ia < kQ1; ++ia)
 #pragma unroll
     for (int ib = 0; ib < kQ1; ++ib) {
       const int i = 5 * ia + ib;
-      const float lf = a.lam_in[(size_t)i * a.nv + v];
-      const float lg = has_g ? a.lam_in[(size_t)(kQ + i) * a.nv + v] : 0.f;
+      const float lf = lfv[i];
+      const float lg = lgv[i];
       float E, Eux, Euy, Eq;
       eq_point<float>(d, ia, ib, &E, &Eux, &Euy, &Eq);
       const float w = a.cs.wf[ia] * a.cs.wf[ib];
@@ -119,8 +126,8 @@ __global__ void __launch_bounds__(128) adjoint_collide_kernel(const __grid_const
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const float cx = a.cs.xif[i / 5], cy = a.cs.xif[i % 5];
-    const float lf = a.lam_in[(size_t)i * a.nv + v];
-    const float lg = a.lam_in[(size_t)(kQ + i) * a.nv + v];
+    const float lf = lfv[i];
+    const float lg = lgv[i];
     a.mu[(size_t)i * a.nv + v] =
         make_float2((1.f - om) * lf + om * (z0 + z1 * cx + z2 * cy + z3 * (cx * cx + cy * cy)),
                     has_g ? (1.f - om) * lg + om * z3 : 0.f);
@@ -185,6 +192,98 @@ __global__ void __launch_bounds__(256) adjoint_stream_y_kernel(const __grid_cons
   }
 }
 
+// S^T on a uniform grid in one pass: a block takes a 32 x 32 tile of target vertices of one
+// velocity plane, loads the source region the transposed stencils reach (the tile and a halo of
+// H vertices on every side, wrapped on periodic axes) into shared memory, applies the x stencils
+// to every row of the region, then the y stencils to the tile.  Small blocks (one plane, few
+// registers) keep eight of them resident per SM, which hides the region loads.  The entries of each stencil are
+// the same as in the two-pass form and summed in the same order.
+constexpr int kAT = 32;   // target tile edge of the fused S^T
+
+// Index of region row/column j on an axis of n vertices: wrapped on periodic axes (the region
+// may reach several periods round on very small grids), clamped otherwise (clamped cells are
+// loaded but never read: transposed stencils of non-periodic axes stay inside the axis).
+__device__ __forceinline__ int wrap_or_clamp(int j, int n, int periodic) {
+  if (periodic) {
+    if (j < 0) j += n;
+    if (j >= n) j -= n;
+    if (j < 0 || j >= n) j = ((j % n) + n) % n;   // grids smaller than the region
+    return j;
+  }
+  return j < 0 ? 0 : (j >= n ? n - 1 : j);
+}
+
+template <int KW, int H>
+__global__ void __launch_bounds__(256) adjoint_stream_fused_kernel(const __grid_constant__ AdjointArgs a) {
+  constexpr int RX = kAT + 2 * H, RY = kAT + 2 * H;
+  __shared__ float2 Sm[RY][RX];    // source region: rows y0-H.., columns x0-H..
+  __shared__ float2 Tm[RY][kAT];   // after the x stencils
+  __shared__ int Yo[kAT][KW];      // y stencils of the tile's rows: source row - target row
+  __shared__ float Yw[kAT][KW];
+  __shared__ int Yd[kAT];
+  const int i = blockIdx.z, ia = i / 5, ib = i % 5;
+  const int x0 = blockIdx.x * kAT, y0 = blockIdx.y * kAT;
+  const float2* m = a.mu + (size_t)i * a.nv;
+  for (int e = threadIdx.x; e < RX * RY; e += 256) {
+    const int r = e / RX, cc = e - r * RX;
+    const int gy = wrap_or_clamp(y0 - H + r, a.ny, a.periodic_y);
+    const int gx = wrap_or_clamp(x0 - H + cc, a.nx, a.periodic_x);
+    Sm[r][cc] = __ldg(m + (size_t)gy * a.nx + gx);
+  }
+  for (int e = threadIdx.x; e < kAT * KW; e += 256) {
+    const int rr = e / KW, k = e - rr * KW, w = y0 + rr;
+    if (w < a.ny) {
+      const size_t q = ((size_t)ib * a.ny + w) * KW + k;
+      Yo[rr][k] = __ldg(a.ty_rel + q);
+      Yw[rr][k] = __ldg(a.ty_w + q);
+      if (k == 0) Yd[rr] = __ldg(a.ty_deg + (size_t)ib * a.ny + w);
+    }
+  }
+  // the target column's transposed x stencil, as positions in a region row
+  const int c = threadIdx.x & 31, u = x0 + c;
+  int xo[KW];
+  float xw[KW];
+  const int xdeg = u < a.nx ? __ldg(a.tx_deg + (size_t)ia * a.nx + u) : 0;
+#pragma unroll
+  for (int k = 0; k < KW; ++k) {
+    const bool on = k < xdeg;
+    const size_t q = ((size_t)ia * a.nx + (on ? u : 0)) * KW + k;
+    xo[k] = H + c + (on ? __ldg(a.tx_rel + q) : 0);
+    xw[k] = on ? __ldg(a.tx_w + q) : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x >> 5; r < RY; r += 8) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < KW; ++k)
+      if (k < xdeg) acc = fma2(bcast2(xw[k]), Sm[r][xo[k]], acc);
+    Tm[r][c] = acc;
+  }
+  __syncthreads();
+  if (u >= a.nx) return;
+  for (int rr = threadIdx.x >> 5; rr < kAT; rr += 8) {
+    const int w = y0 + rr;
+    if (w >= a.ny) break;
+    const int deg = Yd[rr];
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < KW; ++k)
+      if (k < deg) acc = fma2(bcast2(Yw[rr][k]), Tm[H + rr + Yo[rr][k]][c], acc);
+    const size_t t = (size_t)w * a.nx + u;
+    a.lam_out[(size_t)i * a.nv + t] = acc.x;
+    a.lam_out[(size_t)(kQ + i) * a.nv + t] = (a.cp.npop == 2) ? acc.y : 0.f;
+  }
+}
+
+template <int KW>
+static void launch_fused_kw(const AdjointArgs& a, cudaStream_t s) {
+  const dim3 grid((unsigned)((a.nx + kAT - 1) / kAT), (unsigned)((a.ny + kAT - 1) / kAT), kQ);
+  if (a.halo <= 4)
+    adjoint_stream_fused_kernel<KW, 4><<<grid, 256, 0, s>>>(a);
+  else
+    adjoint_stream_fused_kernel<KW, 8><<<grid, 256, 0, s>>>(a);
+}
+
 // S^T on a mapped grid: CSR over the target vertex, per velocity.
 __global__ void __launch_bounds__(256) adjoint_stream_mapped_kernel(const __grid_constant__ AdjointArgs a) {
   const int x = blockIdx.x * 256 + threadIdx.x, i = blockIdx.z;
@@ -207,6 +306,14 @@ cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
   const dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)(a.ny < 65535 ? a.ny : 65535), kQ);
   if (a.mapped) {
     adjoint_stream_mapped_kernel<<<grid, 256, 0, s>>>(a);
+  } else if (a.halo <= 8 && (a.ny + kAT - 1) / kAT <= 65535) {
+    switch (a.kw) {   // one pass: x and y stencils through shared memory
+      case 4: launch_fused_kw<4>(a, s); break;
+      case 8: launch_fused_kw<8>(a, s); break;
+      case 12: launch_fused_kw<12>(a, s); break;
+      case 16: launch_fused_kw<16>(a, s); break;
+      default: return cudaErrorInvalidValue;
+    }
   } else {
     const dim3 gx(grid.x, (unsigned)((a.ny + 15) / 16 < 65535 ? (a.ny + 15) / 16 : 65535), kQ);
     switch (a.kw) {   // x: 16 rows per thread, the column's stencil loaded once

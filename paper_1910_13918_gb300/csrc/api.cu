@@ -45,6 +45,7 @@ struct sllbm_ctx {
   int cur = 0;
   bool precomputed = false, initialized = false;
   int kernel = kKernelGather;
+  int q9_tma = 0;                        // D2Q9 FP32 uniform: the TMA-staged kernel
   // uniform tables
   int *offx = nullptr, *offy = nullptr;
   float *wx = nullptr, *wy = nullptr;
@@ -72,6 +73,8 @@ struct sllbm_ctx {
   bool transposed = false;
   float* mu = nullptr;
   int *tx_col = nullptr, *ty_col = nullptr, tkw = 0;   // fixed-width transposed stencils
+  int thalo = 0;                                        // their largest source-target offset
+  int *tx_rel = nullptr, *ty_rel = nullptr;             // and each entry's offset
   int *tx_deg = nullptr, *ty_deg = nullptr;
   float2* atmp = nullptr;                               // between the x and y passes of S^T
   float *tx_w = nullptr, *ty_w = nullptr;
@@ -231,6 +234,10 @@ static StepArgs step_args(sllbm_ctx* c, const void* src, void* dst) {
   a.offy_min = c->offy_lo;
   a.offy_max = c->offy_hi;
   a.ghost = c->ghost;
+  a.q9_tma = c->q9_tma;
+  a.gx = c->gx;
+  a.gy = c->gy;
+  a.rows_alloc = c->rows_alloc;
   return a;
 }
 
@@ -301,12 +308,14 @@ static sllbm_status build_uniform_pattern(sllbm_ctx* c) {
   TRY(axis_pattern(c, c->ax, c->offx, c->wx64, false, sx, &okx));
   TRY(axis_pattern(c, c->ay, c->offy, c->wy64, true, sy, &oky));
   if (!okx || !oky) return SLLBM_OK;
-  // The fused kernel's y pass takes each stencil as a whole cell: start offset -l at local node
-  // l, or -P at node 0 (a departure into the cell before).  Anything else goes to the gather path.
+  // The fused kernel takes each stencil as a whole cell, on both axes: start offset -l at local
+  // node l, or -P at node 0 (a departure into the cell before).  Anything else goes to the
+  // gather path.
   for (int comp = 0; comp < kQ1; ++comp)
     for (int k = 0; k < c->P; ++k) {
-      const int d = c->ut.dy_pat[comp][k];
-      if (k == 0 ? (d != 0 && d != -c->P) : d != -k) return SLLBM_OK;
+      const int dy = c->ut.dy_pat[comp][k], dx = c->ut.dx_pat[comp][k];
+      if (k == 0 ? (dy != 0 && dy != -c->P) : dy != -k) return SLLBM_OK;
+      if (k == 0 ? (dx != 0 && dx != -c->P) : dx != -k) return SLLBM_OK;
     }
   if (!c->std_x) {
     TRY(dalloc(c, &c->std_x, (size_t)c->nx));
@@ -325,9 +334,6 @@ static sllbm_status build_uniform_pattern(sllbm_ctx* c) {
   }
   c->ut.std_x = c->std_x;
   c->ut.std_y = c->std_y;
-  // tile height: 8-row tiles (two CTAs per SM) unless SLLBM_UNIFORM_TILE=16 asks for 16-row ones
-  const char* tile = getenv("SLLBM_UNIFORM_TILE");
-  c->ut.tall = tile && atoi(tile) == 16;
   c->ut.gx = c->gx;
   c->ut.gy = c->gy;
   c->ut.rows_alloc = c->rows_alloc;
@@ -779,7 +785,14 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
     TRY(build_mapped_tiles(c));
     if (c->mt.valid) c->kernel = kKernelMapped;
   }
-  c->ghost.on = (c->kernel == kKernelUniform || c->kernel == kKernelMapped) && (c->ax.periodic || c->ay.periodic);
+  c->q9_tma = 0;
+  if (c->kernel == kKernelQ9 && c->store == kStoreF32 && !mapped) {
+    StepArgs a = step_args(c, c->state[0], c->state[1]);
+    a.mapped = 0;
+    c->q9_tma = q9_tma_usable(a) ? 1 : 0;
+  }
+  c->ghost.on = (c->kernel == kKernelUniform || c->kernel == kKernelMapped || c->q9_tma) &&
+                (c->ax.periodic || c->ay.periodic);
   double glx[8], glw[8];
   const int ngl = c->P + 3;
   gauss_legendre01(ngl, glx, glw);
@@ -819,8 +832,9 @@ sllbm_status sllbm_init_equilibrium(sllbm_ctx* c, const double* rho, const doubl
   return SLLBM_OK;
 }
 
-static cudaError_t enqueue_step(sllbm_ctx* c) {
+static cudaError_t enqueue_step(sllbm_ctx* c, float* mom = nullptr) {
   StepArgs a = step_args(c, c->state[c->cur], c->state[c->cur ^ 1]);
+  a.mom = mom;
   cudaError_t e;
   switch (c->kernel) {
     case kKernelUniform:
@@ -853,6 +867,14 @@ sllbm_status sllbm_step(sllbm_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return fail(c, SLLBM_ERR_ARG, "bad arguments");
   if (!c->precomputed || !c->initialized) return fail(c, SLLBM_ERR_STATE, "precompute and init first");
   for (int k = 0; k < nsteps; ++k) CUDA_TRY(c, enqueue_step(c));
+  return SLLBM_OK;
+}
+
+sllbm_status sllbm_step_moments(sllbm_ctx* c, float* moments) {
+  if (!c || !moments) return fail(c, SLLBM_ERR_ARG, "null pointer");
+  if (c->nq1 != kQ1) return fail(c, SLLBM_ERR_UNSUPPORTED, "the moments epilogue covers the D2Q25 set");
+  if (!c->precomputed || !c->initialized) return fail(c, SLLBM_ERR_STATE, "precompute and init first");
+  CUDA_TRY(c, enqueue_step(c, moments));
   return SLLBM_OK;
 }
 
@@ -938,6 +960,7 @@ sllbm_status sllbm_moments(sllbm_ctx* c, float* rho, float* u, float* v, float* 
 struct AxisTranspose {
   std::vector<std::vector<std::pair<int, float>>> rows;   // [comp * n + j]
   size_t max_deg = 0;
+  int max_offset = 0;   // largest |vertex - node| over all entries (the short way round if periodic)
 };
 
 static sllbm_status axis_transpose(sllbm_ctx* c, const AxisK& ax, const int* off_dev, const double* w_dev,
@@ -956,13 +979,24 @@ static sllbm_status axis_transpose(sllbm_ctx* c, const AxisK& ax, const int* off
         t->rows[(size_t)comp * n + src].push_back({j, (float)w[((size_t)comp * n + j) * (P + 1) + k]});
       }
   for (const auto& r : t->rows) t->max_deg = std::max(t->max_deg, r.size());
+  for (size_t r = 0; r < t->rows.size(); ++r)
+    for (const auto& e : t->rows[r]) {
+      int d = e.first - (int)(r % n);
+      if (ax.periodic) {
+        if (d > n / 2) d -= n;
+        if (d < -n / 2) d += n;
+      }
+      t->max_offset = std::max(t->max_offset, d < 0 ? -d : d);
+    }
   return SLLBM_OK;
 }
 
 // Fixed-width copy of a transpose: kw entries per (comp, node), padded with weight 0 on the node.
-static sllbm_status upload_transpose(sllbm_ctx* c, const AxisTranspose& t, int n, int kw, int** col_dev,
-                                     float** w_dev, int** deg_dev) {
-  std::vector<int> col(t.rows.size() * kw), deg(t.rows.size());
+// Also the entries' source - target offsets (the short way round a periodic axis), for the
+// one-pass S^T that reads sources from a region around the target tile.
+static sllbm_status upload_transpose(sllbm_ctx* c, const AxisTranspose& t, int n, bool periodic, int kw,
+                                     int** col_dev, float** w_dev, int** deg_dev, int** rel_dev) {
+  std::vector<int> col(t.rows.size() * kw), deg(t.rows.size()), rel(t.rows.size() * kw, 0);
   std::vector<float> wt(t.rows.size() * kw, 0.f);
   for (size_t r = 0; r < t.rows.size(); ++r) {
     deg[r] = (int)t.rows[r].size();
@@ -970,11 +1004,21 @@ static sllbm_status upload_transpose(sllbm_ctx* c, const AxisTranspose& t, int n
       const bool have = (size_t)k < t.rows[r].size();
       col[r * kw + k] = have ? t.rows[r][k].first : (int)(r % n);
       wt[r * kw + k] = have ? t.rows[r][k].second : 0.f;
+      if (have) {
+        int d = t.rows[r][k].first - (int)(r % n);
+        if (periodic) {
+          if (d > n / 2) d -= n;
+          if (d < -n / 2) d += n;
+        }
+        rel[r * kw + k] = d;
+      }
     }
   }
   TRY(dalloc(c, col_dev, col.size()));
   TRY(dalloc(c, w_dev, wt.size()));
   TRY(dalloc(c, deg_dev, deg.size()));
+  TRY(dalloc(c, rel_dev, rel.size()));
+  CUDA_TRY(c, cudaMemcpy(*rel_dev, rel.data(), rel.size() * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(*col_dev, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(*w_dev, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(*deg_dev, deg.data(), deg.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1062,10 +1106,11 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
       TRY(axis_transpose(c, c->ay, c->offy, c->wy64, &ty));
       const int kw = (int)((std::max(tx.max_deg, ty.max_deg) + 3) / 4 * 4);   // 16-byte rows
       if (kw > 16) return fail(c, SLLBM_ERR_UNSUPPORTED, "adjoint: more than 16 stencils read one node");
-      TRY(upload_transpose(c, tx, c->nx, kw, &c->tx_col, &c->tx_w, &c->tx_deg));
-      TRY(upload_transpose(c, ty, c->ny, kw, &c->ty_col, &c->ty_w, &c->ty_deg));
+      TRY(upload_transpose(c, tx, c->nx, c->ax.periodic, kw, &c->tx_col, &c->tx_w, &c->tx_deg, &c->tx_rel));
+      TRY(upload_transpose(c, ty, c->ny, c->ay.periodic, kw, &c->ty_col, &c->ty_w, &c->ty_deg, &c->ty_rel));
       TRY(dalloc(c, &c->atmp, (size_t)kQ * c->nv));
       c->tkw = kw;
+      c->thalo = std::max(tx.max_offset, ty.max_offset);
     }
     c->transposed = true;
   }
@@ -1088,6 +1133,11 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
   a.ty_w = c->ty_w;
   a.ty_deg = c->ty_deg;
   a.tmp = c->atmp;
+  a.periodic_x = c->ax.periodic;
+  a.periodic_y = c->ay.periodic;
+  a.halo = c->thalo;
+  a.tx_rel = c->tx_rel;
+  a.ty_rel = c->ty_rel;
   a.tm_ptr = c->tm_ptr;
   a.tm_col = c->tm_col;
   a.tm_w = c->tm_w;

@@ -46,13 +46,19 @@ struct StepArgs {
   const int* vlist;
   long long nlist;
   GhostK ghost;         // periodic images to keep up to date in the ghost cells
+  // optional: (rho, u, v, theta) of each vertex's collision, dense [4][ny][nx] FP32 (plane
+  // stride nv); null to skip
+  float* mom;
+  // D2Q9, FP32 storage on a uniform grid: the TMA-staged kernel (the ghost cells hold the
+  // periodic images, kept by its writes); gx, gy, rows_alloc as in UniformTables
+  int q9_tma;
+  int gx, gy, rows_alloc;
 };
 
 // Cell-periodic pattern of a uniform grid (see step_uniform.cu): per velocity component and
 // local node, the y interpolation as a band of 2p+1 taps around the vertex and the x taps.
 struct UniformTables {
   bool valid;
-  bool tall;                  // 16-row tiles (one CTA per SM) or 8-row tiles (two per SM)
   double wy_pat[kQ1][4][5];   // [b][l][alpha]
   double wx_pat[kQ1][4][5];   // [a][k][alpha]
   int dy_pat[kQ1][4];         // [b][l]: stencil start - vertex row, in [-p, 0]
@@ -86,12 +92,14 @@ cudaError_t launch_step_gather(const StepArgs& a, int store, cudaStream_t s);
 // Fused shared-memory step for uniform grids (pattern band interpolation); writes only the
 // vertices marked in std_x/std_y.  cudaErrorNotSupported if the tables are not valid.
 cudaError_t launch_step_uniform(const StepArgs& a, const UniformTables& t, int store, cudaStream_t s);
-int uniform_tile_rows(int P, bool tall);
 // Plain FP64 step on full populations.
 cudaError_t launch_step_plain_f64(const StepArgs& a, cudaStream_t s);
 // D2Q9 step (isothermal, one population, planar storage): FP32 arithmetic on FP32/BF16
 // deviations or FP64 on full populations; per-axis tables or, with a.mapped, descriptors.
 cudaError_t launch_step_q9(const StepArgs& a, int store, cudaStream_t s);
+// Whether the TMA-staged D2Q9 kernel can take this uniform grid (its window fits the shared
+// memory and the ghost cells); the host then keeps the periodic images in the ghost cells.
+bool q9_tma_usable(const StepArgs& a);
 
 // ---- precompute (FP64) ----
 struct GeomArgs {
@@ -174,6 +182,10 @@ struct AdjointArgs {
   const float* ty_w;
   const int* ty_deg;   // [5][ny]
   float2* tmp;         // [25][nv] scratch between the x and y passes of the uniform S^T
+  int periodic_x, periodic_y;
+  int halo;            // largest |source - target| of the uniform transposed stencils (wrapped)
+  const int* tx_rel;   // [5][nx][kw]: source - target of each entry, the short way round
+  const int* ty_rel;   // [5][ny][kw]
   const long long* tm_ptr;  // [25][nv+1]
   const int* tm_col;
   const float* tm_w;

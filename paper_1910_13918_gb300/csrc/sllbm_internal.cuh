@@ -229,16 +229,31 @@ __device__ __forceinline__ T eq_em1(const EqFactors<T>& e, int a, int b) {
   return s;
 }
 
+// Moments (rho, u, v, theta) of the pre-collision values of one vertex: what its collision was
+// evaluated at (theta from the moments also in the isothermal configuration, whose equilibrium
+// takes theta = 1).
+struct VertexMoments {
+  float rho, ux, uy, theta;
+};
+
+__device__ __forceinline__ void store_moments(float* mom, long long nv, long long v, const VertexMoments& vm) {
+  mom[v] = vm.rho;
+  mom[nv + v] = vm.ux;
+  mom[2 * nv + v] = vm.uy;
+  mom[3 * nv + v] = vm.theta;
+}
+
 // Collision of one vertex in deviation form, FP32.  fg[i] = (f_i - w_i, g_i - K w_i) before
 // collision (g unused with a single population); on return fg holds the post-collision
-// deviations.  Returns false if the density or temperature is non-positive or non-finite.
+// deviations and vm the moments of the pre-collision values.  Returns false if the density or
+// temperature is non-positive or non-finite.
 //
 // With X_k(a) = A_k(u_x) he[k][a] and S_m(b) = sum_{l=1..m} A_l(u_y) he[l][b] the equilibrium
 // deviation is f_ab^eq - w_ab = w_a w_b (drho + rho S_4(b)) + sum_k (rho w_a X_k(a)) (w_b (1 +
 // S_{4-k}(b))): after a per-vertex set-up of 45 factors, five FMAs per velocity.
 template <bool PR = false>
 __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Consts& cs,
-                                                      const CollideK& cp) {
+                                                      const CollideK& cp, VertexMoments& vm) {
   // moments (Sec. II): rho = 1 + sum fbar, j = sum fbar xi, A2 = sum fbar |xi|^2, G = sum gbar.
   // Row and column sums of the (f, g) pairs in packed FP32x2: rs[a] = (sum_b f_ab, sum_b g_ab).
   float2 rs[kQ1], cl[kQ1];
@@ -306,8 +321,12 @@ __device__ __forceinline__ bool collide_deviation_f32(float2 (&fg)[kQ], const Co
   }
   (void)Qn;
   // theta - 1 = (A2 + G - rho |u|^2 - 2 C_v drho) / (2 C_v rho)
-  const float q = cp.iso ? 0.f
-                        : (a2 + G - rho * (ux * ux + uy * uy) - 2.f * cp.cvf * drho) * inv_rho * cp.inv2cvf;
+  const float qk = (a2 + G - rho * (ux * ux + uy * uy) - 2.f * cp.cvf * drho) * inv_rho * cp.inv2cvf;
+  const float q = cp.iso ? 0.f : qk;
+  vm.rho = rho;
+  vm.ux = ux;
+  vm.uy = uy;
+  vm.theta = 1.f + qk;
   float ax[5], ay[5];
   ax[1] = ux;
   ax[2] = ux * ux + q;

@@ -64,7 +64,15 @@ __global__ void __launch_bounds__(128) step_plain_f64_kernel(const __grid_consta
     e2 += f[i] * (cx * cx + cy * cy) + (npop == 2 ? g[i] : 0.0);
   }
   const double ux = jx / rho, uy = jy / rho;
-  const double theta = a.cp.iso ? 1.0 : (e2 - rho * (ux * ux + uy * uy)) / (2.0 * a.cp.cv * rho);
+  const double theta_k = (e2 - rho * (ux * ux + uy * uy)) / (2.0 * a.cp.cv * rho);
+  const double theta = a.cp.iso ? 1.0 : theta_k;
+  if (a.mom) {
+    const long long v = (long long)iy * a.nx + ix;
+    a.mom[v] = (float)rho;
+    a.mom[a.nv + v] = (float)ux;
+    a.mom[2 * a.nv + v] = (float)uy;
+    a.mom[3 * a.nv + v] = (float)theta_k;
+  }
   const double q = theta - 1.0;
   EqFactors<double> e;
   eq_factors<double>(a.cs.he, ux, uy, q, e);

@@ -68,8 +68,10 @@ __global__ void __launch_bounds__(128) step_gather_kernel(const __grid_constant_
     fg[i] = acc;
   }
   const bool two = a.cp.npop == 2;
-  const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp);
+  VertexMoments vm;
+  const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp, vm);
   if (!ok) atomicOr(a.flag, 1);
+  if (a.mom) store_moments(a.mom, a.nv, (long long)iy * a.nx + ix, vm);
   if (!two) {   // one population: the g slots stay zero
 #pragma unroll
     for (int i = 0; i < kQ; ++i) fg[i].y = 0.f;

@@ -146,9 +146,11 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
         fg[5 * ph + b] = acc;
       }
     }
-    const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp);
+    VertexMoments vm;
+    const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp, vm);
     if (store) {
       if (!ok) atomicOr(a.flag, 1);
+      if (a.mom) store_moments(a.mom, a.nv, (long long)y * a.nx + x, vm);
       Store* dst = static_cast<Store*>(a.dst);
       if (!two) {   // one population: the g slots stay zero
 #pragma unroll

@@ -443,8 +443,185 @@ __global__ void __launch_bounds__(kNT) step_q9_async_kernel(const __grid_constan
   if (!ok) atomicOr(a.flag, 1);
 }
 
+// FP32 storage on uniform grids, persistent CTAs with Tensor Memory Accelerator staging: a tile's
+// window of the 9 planes arrives as three tensor copies (cp.async.bulk.tensor, 3 planes each,
+// one mbarrier each), issued a whole tile ahead into the other of two buffers, so that the copies
+// of the next tile overlap the interpolation and collision of this one, and plane i's
+// interpolation waits only for its own group.  The state's ghost cells hold the periodic images
+// (every write stores them too), so a window never wraps; its origin is rounded down to a
+// 16-byte boundary and the stencil offsets carry the remainder.
+constexpr int kQ9Groups = 3;   // tensor copies per tile (3 planes each)
+
+struct Q9Tma {
+  CUtensorMap tmap;   // 3D: (column, row, plane) over the whole allocation, FP32
+  int ox4;            // window origin relative to the tile origin, rounded down to 4 columns
+  int W4, H;          // window columns (a multiple of 4) and rows
+  int dx;             // ox - ox4: shift of the stencil offsets
+};
+
+// floats of one copy group (3 planes of H x W4), padded to keep every copy 128-byte aligned
+__host__ __device__ inline int q9_group_elems(int W4, int H) { return (3 * H * W4 + 31) / 32 * 32; }
+
+size_t q9_tma_smem_bytes(int W4, int H) {
+  return 128 + sizeof(float) * (2 * (size_t)kQ9Groups * q9_group_elems(W4, H) + (size_t)kTY * W4) +
+         sizeof(uint64_t) * 2 * kQ9Groups;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kNT) step_q9_tma_kernel(const __grid_constant__ StepArgs a,
+                                                           const __grid_constant__ Window win,
+                                                           const __grid_constant__ Q9Tma qt) {
+  extern __shared__ unsigned char q9t_smem[];
+  float* base = reinterpret_cast<float*>(q9t_smem + ((128 - (smem_u32(q9t_smem) & 127)) & 127));
+  const int W4 = qt.W4, H = qt.H;
+  const int plane_elems = H * W4, group_elems = q9_group_elems(W4, H), buf_elems = kQ9Groups * group_elems;
+  float* S = base;                          // [2][3 groups][3][H][W4]
+  float* T = S + 2 * buf_elems;             // [kTY][W4]
+  uint64_t* BAR = reinterpret_cast<uint64_t*>(T + kTY * W4);   // [2][3]; offset a multiple of 8 B
+  const int tid = threadIdx.x, lane = tid & 31, row = tid >> 5;
+  const int tiles_x = (a.nx + 31) / 32;
+  const int ntiles = tiles_x * ((a.ny + kTY - 1) / kTY);
+  if (tid == 0) {
+    for (int k = 0; k < 2 * kQ9Groups; ++k) mbar_init(&BAR[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int tile, int buf) {
+    if (tid != 0 || tile >= ntiles) return;
+    const int tx0 = (tile % tiles_x) * 32, ty0 = (tile / tiles_x) * kTY;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+#pragma unroll
+    for (int g = 0; g < kQ9Groups; ++g) {
+      uint64_t* bar = &BAR[buf * kQ9Groups + g];
+      mbar_expect_tx(bar, (unsigned)(sizeof(float) * 3 * plane_elems));
+      tma_load_3d(S + (size_t)buf * buf_elems + (size_t)g * group_elems, &qt.tmap, a.gx + tx0 + qt.ox4,
+                  a.gy + ty0 + win.oy, 3 * g, bar);
+    }
+  };
+  issue(blockIdx.x, 0);
+  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+#pragma unroll 1
+  for (int k = 0; k < my_tiles; ++k) {
+    const int tile = blockIdx.x + k * gridDim.x, buf = k & 1;
+    const unsigned parity = (unsigned)((k >> 1) & 1);
+    const int tx0 = (tile % tiles_x) * 32, ty0 = (tile / tiles_x) * kTY;
+    const int x = tx0 + lane, y = ty0 + row;
+    __syncthreads();   // every thread is past tile k - 1: its buffer (the other one) is free
+    issue(tile + gridDim.x, buf ^ 1);
+    // taps of this thread's column (x pass) and of its warp's row (y pass), clamped into the grid
+    // for threads past its edge; stencil starts as window column / row
+    const int xc = min(x, a.nx - 1), yc = min(y, a.ny - 1);
+    int xo[kN1], yo[kN1];
+    float xw[kN1][P + 1], yw[kN1][P + 1];
+#pragma unroll
+    for (int c = 0; c < kN1; ++c) {
+      xo[c] = xc + a.offx[c * a.nx + xc] - tx0 - win.ox + qt.dx;
+      yo[c] = yc + a.offy[c * a.ny + yc] - ty0 - win.oy;
+#pragma unroll
+      for (int q = 0; q <= P; ++q) {
+        xw[c][q] = a.wx[(size_t)(c * a.nx + xc) * (P + 1) + q];
+        yw[c][q] = a.wy[(size_t)(c * a.ny + yc) * (P + 1) + q];
+      }
+    }
+    const float* Sb = S + (size_t)buf * buf_elems;
+    float fb[kN];
+#pragma unroll
+    for (int i = 0; i < kN; ++i) {
+      const int ca = i / kN1, cb = i % kN1;
+      if (i % 3 == 0) mbar_wait(&BAR[buf * kQ9Groups + i / 3], parity, a.flag);   // group landed
+      if (i > 0) __syncthreads();   // every thread is past the previous plane's x pass (T free)
+      const float* Si = Sb + (i / 3) * group_elems + (i % 3) * plane_elems;
+#pragma unroll
+      for (int m = 0; m < kCC; ++m) {
+        const int c = lane + 32 * m;
+        if (c < W4) {
+          const float* col = Si + yo[cb] * W4 + c;
+          const float b0 = col[0];
+          float acc = b0;
+#pragma unroll
+          for (int q = 1; q <= P; ++q) acc = fmaf(yw[cb][q], col[q * W4] - b0, acc);
+          T[row * W4 + c] = acc;
+        }
+      }
+      __syncthreads();   // T complete
+      {
+        const float* t = T + row * W4 + xo[ca];
+        const float b0 = t[0];
+        float acc = b0;
+#pragma unroll
+        for (int q = 1; q <= P; ++q) acc = fmaf(xw[ca][q], t[q] - b0, acc);
+        fb[i] = acc;
+      }
+    }
+    if (x < a.nx && y < a.ny) {
+      const bool ok = collide_q9_f32(fb, a.cs, a.cp);
+      if (!ok) atomicOr(a.flag, 1);
+      float* dst = static_cast<float*>(a.dst);
+      store_images(a.ghost, x, y, [&](int xx, int yy) {
+        float* o = dst + (ptrdiff_t)yy * a.pitch + xx;
+#pragma unroll
+        for (int i = 0; i < kN; ++i) o[(size_t)i * a.plane_stride] = fb[i];
+      });
+    }
+  }
+}
+
+// Window of the TMA kernel for a uniform grid, or false if the kernel cannot take it (the
+// window, rounded to 16-byte columns, must fit the shared memory and stay inside the ghost cells).
+bool q9_tma_window(const StepArgs& a, Window* win, Q9Tma* qt) {
+  if (a.mapped || a.xs != 1) return false;
+  *win = Window{a.offx_min, a.offy_min, 32 + a.offx_max - a.offx_min, kTY + a.offy_max - a.offy_min};
+  const int ox4 = (win->ox >= 0) ? win->ox / 4 * 4 : -((-win->ox + 3) / 4 * 4);
+  qt->ox4 = ox4;
+  qt->dx = win->ox - ox4;
+  qt->W4 = (win->W + qt->dx + 3) / 4 * 4;
+  qt->H = win->H;
+  if (qt->W4 > kMaxW || qt->H > kMaxH || qt->H > 256) return false;
+  // first and last window column / row of any tile, against the allocation's ghost cells
+  const int tiles_x = (a.nx + 31) / 32, tiles_y = (a.ny + kTY - 1) / kTY;
+  if (ox4 < -a.gx || (tiles_x - 1) * 32 + ox4 + qt->W4 > a.pitch - a.gx) return false;
+  if (win->oy < -a.gy || (tiles_y - 1) * kTY + win->oy + qt->H > a.rows_alloc - a.gy) return false;
+  return q9_tma_smem_bytes(qt->W4, qt->H) <= 200 * 1024;
+}
+
+template <int P>
+static cudaError_t launch_q9_tma(const StepArgs& a, const Window& win, Q9Tma qt, cudaStream_t s) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  const float* alloc = static_cast<const float*>(a.src) - ((ptrdiff_t)a.gy * a.pitch + a.gx);
+  const cuuint64_t dims[3] = {(cuuint64_t)a.pitch, (cuuint64_t)a.rows_alloc, (cuuint64_t)kN};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.pitch * sizeof(float), (cuuint64_t)a.plane_stride * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)qt.W4, (cuuint32_t)qt.H, 3u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  if (enc(&qt.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(alloc), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  const size_t smem = q9_tma_smem_bytes(qt.W4, qt.H);
+  cudaError_t e = cudaFuncSetAttribute(step_q9_tma_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, n_sm = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_q9_tma_kernel<P>, kNT, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int ntiles = ((a.nx + 31) / 32) * ((a.ny + kTY - 1) / kTY);
+  const int grid = ntiles < n_sm * per_sm ? ntiles : n_sm * per_sm;   // persistent CTAs
+  step_q9_tma_kernel<P><<<grid, kNT, smem, s>>>(a, win, qt);
+  return cudaGetLastError();
+}
+
 template <int P, typename Store>
 cudaError_t launch_ps(const StepArgs& a, cudaStream_t s) {
+  if constexpr (std::is_same<Store, float>::value) {
+    if (a.q9_tma) {   // chosen (and the ghost images kept) by the host set-up
+      Window win;
+      Q9Tma qt;
+      if (!q9_tma_window(a, &win, &qt)) return cudaErrorNotSupported;
+      return launch_q9_tma<P>(a, win, qt, s);
+    }
+  }
   if constexpr (!std::is_same<Store, double>::value) {
     // uniform grid whose stencil window fits the staging buffer: the tiled kernel
     const Window win{a.offx_min, a.offy_min, 32 + a.offx_max - a.offx_min, kTY + a.offy_max - a.offy_min};
@@ -485,6 +662,12 @@ cudaError_t launch_store(const StepArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+bool q9_tma_usable(const StepArgs& a) {
+  Window win;
+  Q9Tma qt;
+  return q9_tma_window(a, &win, &qt);
+}
 
 cudaError_t launch_step_q9(const StepArgs& a, int store, cudaStream_t s) {
   if (a.cs.nq1 != kN1 || a.cp.npop != 1 || a.xs != 1 || a.nv == 0) return cudaErrorInvalidValue;

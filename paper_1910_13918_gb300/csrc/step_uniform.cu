@@ -14,7 +14,7 @@
 // velocity plane and vertex) and every interpolation step moves and combines the pair at once:
 // 64-bit shared-memory and global accesses, packed FP32x2 FMAs.
 //
-// Persistent CTAs (two per SM by default, or one with the tall tile) walk over tiles of 32 x TY
+// Persistent CTAs (two per SM) walk over tiles of 32 x TY
 // vertices (TY a multiple of p), one vertex per thread.  The 25 pair planes of a tile are done in
 // 5 stages, one per x component a.  A stage (the 5 planes b = 0..4) is copied into shared memory by one TMA tensor copy (tile +
 // stencil halo; the state layout carries ghost cells with the periodic images, so a tile never
@@ -31,6 +31,8 @@
 // (with the FP32-rounded weights themselves the deficit of their sum would bias every uniform
 // region the same way every step, a systematic mass drift), and in the y pass the differences of
 // a staged column are formed once and shared by all the rows that read them.
+#include <atomic>
+
 #include "kernels.h"
 #include "tma.cuh"
 
@@ -45,18 +47,17 @@ namespace {
 // therefore reach from y0 - p (D = -p at the tile's first row) to y0 + TY (the last cell of the
 // tile), and the start row of every stencil is a cell boundary.
 //
-// Tile of 32 x TY vertices: the "short" tile (8 rows, 6 for p = 3, two CTAs of 32 TY threads per
-// SM; the default: one CTA's barriers and collision burst overlap the other's interpolation) or
-// the "tall" one (16 rows, 12 for p = 3, one CTA per SM).  A y-pass task covers RC = TY / NH rows
-// of one staged column (the whole column, or half of it in the tall tile), from a window of
-// RW = RC + p + 1 rows.
-template <int P, bool Tall>
+// Tile of 32 x TY vertices, TY = 8 (6 for p = 3), two CTAs of 32 TY threads per SM: one CTA's
+// barriers and collision burst overlap the other's interpolation (one CTA of twice the rows per
+// SM measured slower at p = 3 and 4).  A y-pass task covers RC = TY / NH rows of one staged
+// column (NH = 1: the whole column), from a window of RW = RC + p + 1 rows.
+template <int P>
 struct TileShape {
-  static constexpr int TY = Tall ? ((P == 3) ? 12 : 16) : ((P == 3) ? 6 : 8);
+  static constexpr int TY = (P == 3) ? 6 : 8;
   static constexpr int NT = 32 * TY;
-  static constexpr int MINB = Tall ? 1 : 2;      // CTAs per SM
+  static constexpr int MINB = 2;                 // CTAs per SM
   static constexpr int R = TY + P + 1;           // staged rows y0-P .. y0+TY
-  static constexpr int NH = Tall ? 2 : 1;        // row chunks per staged column
+  static constexpr int NH = 1;                   // row chunks per staged column
   static constexpr int RC = TY / NH;             // rows per y-pass task (a multiple of P)
   static constexpr int RW = RC + P + 1;          // window rows per y-pass task
   static_assert(RC % P == 0, "row chunks must hold whole periods of the pattern");
@@ -70,16 +71,18 @@ constexpr int kC = 32 + 2 * kCO;   // staged columns
 // shared-memory bank.  With a gap every 16 columns (P = 4, 2, 1) or two every 17 (P = 3) the
 // x-pass reads of each tap and the y-pass row stores are free of bank conflicts.
 template <int P>
-__host__ __device__ constexpr int tpos(int c) { return P == 3 ? c + 2 * (c / 17) : c + (c >> 4); }
+__host__ __device__ constexpr int tpos(int c) {
+  return P == 3 ? c + 2 * (c / 17) : (P == 1 ? c + (c >> 4) : c + 2 * (c >> 4));
+}
 template <int P>
 struct TRow { static constexpr int N = tpos<P>(kC - 1) + 1; };   // T row length (pairs)
 // ints of the DX [5][P] and EY [5] tables, rounded up to keep the mbarriers 8-byte aligned
 __host__ __device__ constexpr int table_ints(int P) { return (kQ1 * P + kQ1 + 1) / 2 * 2; }
 
 // Elements of one TMA box (5 planes x R rows x C columns x 2 populations), padded to 128 bytes.
-template <int P, bool Tall, typename Store>
+template <int P, typename Store>
 struct BoxShape {
-  static constexpr int ELEMS = 5 * TileShape<P, Tall>::R * kC * 2;
+  static constexpr int ELEMS = 5 * TileShape<P>::R * kC * 2;
   static constexpr int BYTES = ELEMS * (int)sizeof(Store);
   static constexpr int STRIDE = ((BYTES + 127) / 128) * 128 / (int)sizeof(Store);
 };
@@ -116,60 +119,75 @@ __device__ __forceinline__ void y_rows(const float2 (&win)[RW], const float2 (&d
   }
 }
 
-// y pass of one stage: task = (plane b, row chunk h, staged column c).  The first 5*NH*32 tasks
-// give each warp one (b, h) and 32 columns; the right-hand C-32 columns of the NH chunks of a
-// plane b go to one more warp per b (NH*(C-32) of its lanes) when the block has the warps, so
-// that the branch on the plane's cell choice never diverges; otherwise they are packed.
-template <int P, bool Tall, typename Store>
-__device__ __forceinline__ void y_pass(const Store* __restrict__ Sst, float2* __restrict__ Tst,
-                                    const float2* __restrict__ WY, const int* __restrict__ EY) {
-  using TS = TileShape<P, Tall>;
-  constexpr int TY = TS::TY, R = TS::R, NH = TS::NH, RC = TS::RC, RW = TS::RW, NT = TS::NT;
+// y pass: task = (plane b, row chunk h, staged column c).  The first 5*NH*32 tasks give each
+// warp one (b, h) and 32 columns; the right-hand 2P columns of the NH chunks of a plane b go to
+// one more warp per b (NH*2P of its lanes) when the block has the warps, so that the branch on
+// the plane's cell choice never diverges; otherwise they are packed.  A block never has more
+// tasks than threads, so a thread's task is the same in every stage: it is set up once.
+struct YTask {
+  int src;    // element offset of the task's first window row in a staging buffer
+  int dst;    // pair offset of its first output in a T buffer
+  int b;      // plane (y component)
+};
+
+template <int P>
+__device__ __forceinline__ bool y_task(int t, YTask& yt) {
+  using TS = TileShape<P>;
+  constexpr int TY = TS::TY, R = TS::R, NH = TS::NH, RC = TS::RC, NT = TS::NT;
   // The x pass reads staged columns [4 - P, 36 + P) only (stencil starts in [-P, 0] from the
   // column, P + 1 taps): 32 columns per plane in the warp tasks, the 2P others in the packed ones.
   constexpr int C0 = kCO - P;
   constexpr int CR = 2 * P;
   static_assert(NH * CR <= 32, "right-hand columns of one plane must fit in a warp");
-  // right-hand columns: one warp per plane b if the block has the warps, else packed
   constexpr bool kSpread = kQ1 * (NH + 1) * 32 <= NT;
   constexpr int kTasks = kSpread ? kQ1 * (NH + 1) * 32 : kQ1 * NH * (32 + CR);
-  const int tid = threadIdx.x;
-#pragma unroll 1
-  for (int t = tid; t < kTasks; t += NT) {
-    int b, h, c;
-    if (t < kQ1 * NH * 32) {
-      const int g = t >> 5;
-      b = g / NH;
-      h = g - b * NH;
-      c = C0 + (t & 31);
-    } else if (kSpread) {
-      const int u = t - kQ1 * NH * 32, lane = u & 31;
-      if (lane >= NH * CR) continue;
-      b = u >> 5;
-      h = lane / CR;
-      c = C0 + 32 + lane - h * CR;
-    } else {
-      const int u = t - kQ1 * NH * 32;
-      b = u / (NH * CR);
-      const int r = u - b * NH * CR;
-      h = r / CR;
-      c = C0 + 32 + r - h * CR;
-    }
-    const Store* col = Sst + ((size_t)(b * R + h * RC) * kC + c) * 2;
-    float2 win[RW], dl[RW - 1];
-#pragma unroll
-    for (int j = 0; j < RW; ++j) win[j] = lds_pair(col + j * kC * 2);
-#pragma unroll
-    for (int j = 0; j < RW - 1; ++j) dl[j] = sub2(win[j + 1], win[j]);
-    float2* tout = Tst + ((size_t)b * TY + h * RC) * TRow<P>::N + tpos<P>(c);
-    float2 W[P][P];   // tail sums of the plane's P row classes, in registers
-#pragma unroll
-    for (int l = 0; l < P; ++l) load_taps<P>(WY + (b * P + l) * 4, W[l]);
-    if (EY[b])
-      y_rows<P, RC, RW, true>(win, dl, W, tout);
-    else
-      y_rows<P, RC, RW, false>(win, dl, W, tout);
+  static_assert(kTasks <= NT, "one y-pass task per thread at most");
+  if (t >= kTasks) return false;
+  int b, h, c;
+  if (t < kQ1 * NH * 32) {
+    const int g = t >> 5;
+    b = g / NH;
+    h = g - b * NH;
+    c = C0 + (t & 31);
+  } else if (kSpread) {
+    const int u = t - kQ1 * NH * 32, lane = u & 31;
+    if (lane >= NH * CR) return false;
+    b = u >> 5;
+    h = lane / CR;
+    c = C0 + 32 + lane - h * CR;
+  } else {
+    const int u = t - kQ1 * NH * 32;
+    b = u / (NH * CR);
+    const int r = u - b * NH * CR;
+    h = r / CR;
+    c = C0 + 32 + r - h * CR;
   }
+  yt.src = ((b * R + h * RC) * kC + c) * 2;
+  yt.dst = (b * TY + h * RC) * TRow<P>::N + tpos<P>(c);
+  yt.b = b;
+  return true;
+}
+
+template <int P, typename Store>
+__device__ __forceinline__ void y_pass(const Store* __restrict__ Sst, float2* __restrict__ Tst,
+                                    const float2* __restrict__ WY, const int* __restrict__ EY,
+                                    const YTask& yt) {
+  using TS = TileShape<P>;
+  constexpr int RC = TS::RC, RW = TS::RW;
+  const Store* col = Sst + yt.src;
+  float2 win[RW], dl[RW - 1];
+#pragma unroll
+  for (int j = 0; j < RW; ++j) win[j] = lds_pair(col + j * kC * 2);
+#pragma unroll
+  for (int j = 0; j < RW - 1; ++j) dl[j] = sub2(win[j + 1], win[j]);
+  float2* tout = Tst + yt.dst;
+  float2 W[P][P];   // tail sums of the plane's P row classes, in registers
+#pragma unroll
+  for (int l = 0; l < P; ++l) load_taps<P>(WY + (yt.b * P + l) * 4, W[l]);
+  if (EY[yt.b])
+    y_rows<P, RC, RW, true>(win, dl, W, tout);
+  else
+    y_rows<P, RC, RW, false>(win, dl, W, tout);
 }
 
 }  // namespace
@@ -192,11 +210,11 @@ struct UniformArgs {
   int gx, gy;                            // ghost columns / rows before the interior origin
 };
 
-template <int P, typename Store, bool Tall, bool PR>
-__global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MINB)
+template <int P, typename Store, bool PR>
+__global__ void __launch_bounds__(TileShape<P>::NT, TileShape<P>::MINB)
     step_uniform_kernel(const __grid_constant__ UniformArgs<P> ua) {
-  using TS = TileShape<P, Tall>;
-  using BS = BoxShape<P, Tall, Store>;
+  using TS = TileShape<P>;
+  using BS = BoxShape<P, Store>;
   constexpr int TY = TS::TY, NT = TS::NT;
   constexpr int NSB = kStageBuffers;   // stage k lands in S[k % NSB], issued NSB-1 stages ahead
   constexpr int PD = NSB - 1;
@@ -244,6 +262,8 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
     }
   };
 
+  YTask yt;
+  const bool yon = y_task<P>(tid, yt);
 #pragma unroll
   for (int k = 0; k < PD; ++k) issue(blockIdx.x, k, k);
   // Phase s (global stage counter) runs the y pass of stage s and the x pass of stage s - 1; when
@@ -251,7 +271,8 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
   // the y pass of the following tile's first stage: five barriers per tile, and the FMA-heavy
   // collision of some warps overlaps the shared-memory-heavy y pass of others.
   const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  int x = 0, y = 0;   // vertex of the tile in the x pass
+  int x = 0, y = 0, kx = 0;   // vertex of the tile in the x pass and its local node
+  int tpo[P + 1], tpb[P + 1];
   float2 fg[kQ];      // (f, g) after streaming, velocity i = 5a + b
 #pragma unroll 1
   for (int k = 0; k <= my_tiles; ++k) {
@@ -268,46 +289,67 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
           issue(tile, j + PD, s + PD);
         else
           issue(tile + gridDim.x, j + PD - kQ1, s + PD);   // the next tile's first stages
-        y_pass<P, Tall, Store>(S + (size_t)(s % NSB) * BS::STRIDE, T + (size_t)(s & 1) * kQ1 * TY * TRow<P>::N,
-                               WY, EY);
+        if (yon)
+          y_pass<P, Store>(S + (size_t)(s % NSB) * BS::STRIDE,
+                                 T + (size_t)(s & 1) * kQ1 * TY * TRow<P>::N, WY, EY, yt);
       }
       if (k == 0 && j == 0) continue;   // no stage before the first
 
       // ---- x pass of stage s-1 (component st): thread = vertex; taps of (a, x mod p) ----
       const int st = (j + kQ1 - 1) % kQ1;
-      if (j == 1) {   // stage 0 of tile k: this thread's vertex
+      if (j == 1) {   // stage 0 of tile k: this thread's vertex, its local node and stencils
         x = (tile % tiles_x) * 32 + lane;
         y = (tile / tiles_x) * TY + row;
+        kx = x % P;
+        // T positions of the stencil columns: the own cell (start -kx) and, for a vertex at
+        // local node 0, the cell before (start -P); which one a stage takes is DX[st][kx]
+#pragma unroll
+        for (int al = 0; al <= P; ++al) {
+          tpo[al] = tpos<P>(lane + kCO - kx + al);
+          tpb[al] = tpos<P>(lane + kCO - P + al);
+        }
       }
       {
-        const int kx = x % P;
         const float2* w = WX + (st * P + kx) * 4;
-        const int cbase = lane + kCO + DX[st * P + kx];
+        const bool before = DX[st * P + kx] != -kx;   // only at kx = 0, start -P
         float2 W[P];
         load_taps<P>(w, W);
         int tp[P + 1];   // T positions of the stencil columns
 #pragma unroll
-        for (int al = 0; al <= P; ++al) tp[al] = tpos<P>(cbase + al);
+        for (int al = 0; al <= P; ++al) tp[al] = before ? tpb[al] : tpo[al];
         const float2* trow0 = T + ((size_t)((s - 1) & 1) * kQ1 * TY + row) * TRow<P>::N;
 #pragma unroll
         for (int b = 0; b < kQ1; ++b) {
           const float2* trow = trow0 + b * TY * TRow<P>::N;
-          float2 prev = trow[tp[0]], acc = prev;
+          float2 v[P + 1];
+          if constexpr (P == 2 || P == 4) {
+            // even P: stencils start on a cell boundary, an even staged column, and the skew
+            // moves columns by whole 16-byte units: two taps per 16-byte load
 #pragma unroll
-          for (int al = 1; al <= P; ++al) {
-            const float2 cur = trow[tp[al]];
-            acc = fma2(W[al - 1], sub2(cur, prev), acc);
-            prev = cur;
+            for (int al = 0; al + 1 <= P; al += 2) {
+              const float4 q = *reinterpret_cast<const float4*>(trow + tp[al]);
+              v[al] = make_float2(q.x, q.y);
+              v[al + 1] = make_float2(q.z, q.w);
+            }
+            v[P] = trow[tp[P]];
+          } else {
+#pragma unroll
+            for (int al = 0; al <= P; ++al) v[al] = trow[tp[al]];
           }
+          float2 acc = v[0];
+#pragma unroll
+          for (int al = 1; al <= P; ++al) acc = fma2(W[al - 1], sub2(v[al], v[al - 1]), acc);
           fg[5 * st + b] = acc;
         }
       }
       if (j != 0) continue;
 
       // ---- the tile of the x pass is complete: collide and store ----
-      const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp);
+      VertexMoments vm;
+      const bool ok = collide_deviation_f32<PR>(fg, a.cs, a.cp, vm);
       if (x < a.nx && y < a.ny && ua.std_x[x] && ua.std_y[y]) {
         if (!ok) atomicOr(a.flag, 1);
+        if (a.mom) store_moments(a.mom, a.nv, (long long)y * a.nx + x, vm);
         Store* dst = static_cast<Store*>(a.dst);
         if (!two) {   // one population: the g slots stay zero
 #pragma unroll
@@ -326,17 +368,26 @@ __global__ void __launch_bounds__(TileShape<P, Tall>::NT, TileShape<P, Tall>::MI
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
-template <int P, typename Store, bool Tall>
+// SM count of a device, cached per device.
+static int sm_count(int dev) {
+  static std::atomic<int> cache[64];
+  int n = (dev >= 0 && dev < 64) ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+template <int P, typename Store>
 static size_t smem_bytes() {
-  using TS = TileShape<P, Tall>;
-  using BS = BoxShape<P, Tall, Store>;
+  using TS = TileShape<P>;
+  using BS = BoxShape<P, Store>;
   return 128 + sizeof(Store) * kStageBuffers * BS::STRIDE + sizeof(float2) * 2 * kQ1 * TS::TY * TRow<P>::N +
          sizeof(float2) * 2 * kQ1 * P * 4 + sizeof(int) * table_ints(P) + sizeof(uint64_t) * kStageBuffers;
 }
 
-template <int P, typename Store, bool Tall, bool PR>
+template <int P, typename Store, bool PR>
 static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStream_t s) {
-  using TS = TileShape<P, Tall>;
+  using TS = TileShape<P>;
   if (a.xs != 2 || a.ps != 1) return cudaErrorNotSupported;   // interleaved (f, g) pairs only
   UniformArgs<P> ua;
   memset(&ua, 0, sizeof(ua));
@@ -354,8 +405,11 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
         ua.pat.wy[c][l][j] = (float)ty;
       }
       ua.pat.dx[c][l] = t.dx_pat[c][l];
-      // y stencils: D = -l, or D in {0, -P} at l = 0 (checked when the tables were built)
+      // stencils are whole cells: D = -l, or D in {0, -P} at l = 0, on both axes (checked when
+      // the tables were built; the y pass and the x-pass loads rely on it)
       if (l == 0 ? (t.dy_pat[c][0] != 0 && t.dy_pat[c][0] != -P) : t.dy_pat[c][l] != -l)
+        return cudaErrorNotSupported;
+      if (l == 0 ? (t.dx_pat[c][0] != 0 && t.dx_pat[c][0] != -P) : t.dx_pat[c][l] != -l)
         return cudaErrorNotSupported;
     }
     ua.pat.ey[c] = t.dy_pat[c][0] == 0 ? 1 : 0;
@@ -379,54 +433,45 @@ static cudaError_t launch_p(const StepArgs& a, const UniformTables& t, cudaStrea
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  const size_t smem = smem_bytes<P, Store, Tall>();
-  static bool configured = false;  // per template instance
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, Tall, PR>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = smem_bytes<P, Store>();
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  // The shared-memory opt-in is a per-device property of the kernel: set it once per device
+  // (idempotent, so two threads racing on a device's first launch both set the same values).
+  static std::atomic<unsigned long long> configured{0};   // per template instance, bit per device
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (!bit || !(configured.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, PR>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)   // all of the unified L1/shared storage as shared memory
-      e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, Tall, PR>,
+      e = cudaFuncSetAttribute(step_uniform_kernel<P, Store, PR>,
                                cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured.fetch_or(bit, std::memory_order_acq_rel);
   }
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (n_sm <= 0) n_sm = 1;
-  }
+  const int n_sm = sm_count(dev);
   const int ntiles = ((a.nx + 31) / 32) * ((a.ny + TS::TY - 1) / TS::TY);
   const int grid = ntiles < n_sm * TS::MINB ? ntiles : n_sm * TS::MINB;   // persistent CTAs
-  step_uniform_kernel<P, Store, Tall, PR><<<grid, TS::NT, smem, s>>>(ua);
+  step_uniform_kernel<P, Store, PR><<<grid, TS::NT, smem, s>>>(ua);
   return cudaGetLastError();
 }
 
-template <typename Store, bool Tall>
+template <typename Store>
 static cudaError_t launch_store(const StepArgs& a, const UniformTables& t, cudaStream_t s) {
   switch (a.P) {
-    // Pr != 1 runs in the default (short) tile only
-    case 1: return a.cp.pr_on ? launch_p<1, Store, false, true>(a, t, s) : launch_p<1, Store, Tall, false>(a, t, s);
-    case 2: return a.cp.pr_on ? launch_p<2, Store, false, true>(a, t, s) : launch_p<2, Store, Tall, false>(a, t, s);
-    case 3: return a.cp.pr_on ? launch_p<3, Store, false, true>(a, t, s) : launch_p<3, Store, Tall, false>(a, t, s);
-    case 4: return a.cp.pr_on ? launch_p<4, Store, false, true>(a, t, s) : launch_p<4, Store, Tall, false>(a, t, s);
+    case 1: return a.cp.pr_on ? launch_p<1, Store, true>(a, t, s) : launch_p<1, Store, false>(a, t, s);
+    case 2: return a.cp.pr_on ? launch_p<2, Store, true>(a, t, s) : launch_p<2, Store, false>(a, t, s);
+    case 3: return a.cp.pr_on ? launch_p<3, Store, true>(a, t, s) : launch_p<3, Store, false>(a, t, s);
+    case 4: return a.cp.pr_on ? launch_p<4, Store, true>(a, t, s) : launch_p<4, Store, false>(a, t, s);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step_uniform(const StepArgs& a, const UniformTables& t, int store, cudaStream_t s) {
   if (!t.valid) return cudaErrorNotSupported;
-  if (t.tall) {
-    if (store == kStoreBF16) return launch_store<__nv_bfloat16, true>(a, t, s);
-    return launch_store<float, true>(a, t, s);
-  }
-  if (store == kStoreBF16) return launch_store<__nv_bfloat16, false>(a, t, s);
-  return launch_store<float, false>(a, t, s);
-}
-
-int uniform_tile_rows(int P, bool tall) {
-  return tall ? (P == 3 ? 12 : 16) : (P == 3 ? 6 : 8);
+  if (store == kStoreBF16) return launch_store<__nv_bfloat16>(a, t, s);
+  return launch_store<float>(a, t, s);
 }
 
 }  // namespace sllbm

@@ -27,7 +27,7 @@ PRECISIONS = {"f32": PREC_F32, "bf16": PREC_BF16_STORE, "f64": PREC_F64_PLAIN}
 EXPORTS = [
     "sllbm_create", "sllbm_destroy", "sllbm_set_stream", "sllbm_grid_info", "sllbm_state_bytes",
     "sllbm_vertex_coords", "sllbm_vertex_weights", "sllbm_precompute_departures",
-    "sllbm_init_equilibrium", "sllbm_step", "sllbm_step_host", "sllbm_moments", "sllbm_get_state",
+    "sllbm_init_equilibrium", "sllbm_step", "sllbm_step_moments", "sllbm_step_host", "sllbm_moments", "sllbm_get_state",
     "sllbm_set_state", "sllbm_adjoint_step", "sllbm_init_equilibrium_vjp", "sllbm_step_kernel_name",
     "sllbm_launches_per_step", "sllbm_status_string", "sllbm_last_error", "sllbm_moments_noalloc",
     "sllbm3d_create", "sllbm3d_destroy", "sllbm3d_grid_info", "sllbm3d_vertex_coords",
@@ -88,6 +88,7 @@ def load(path: str | None = None):
         "sllbm_precompute_departures": ([P], I),
         "sllbm_init_equilibrium": ([P, V, V, V, V], I),
         "sllbm_step": ([P, I], I),
+        "sllbm_step_moments": ([P, V], I),
         "sllbm_step_host": ([P, V, V, I], I),
         "sllbm_moments": ([P, V, V, V, V, ctypes.POINTER(D)], I),
         "sllbm_get_state": ([P, V], I),
@@ -225,6 +226,12 @@ class SLLBM:
 
     def step(self, n=1):
         self._check(self.lib.sllbm_step(self.h, int(n)))
+
+    def step_moments(self, buf4):
+        """One step writing the (rho, u, v, theta) its collision used into a [4, ny, nx] float32
+        tensor (the saved moments of the adjoint step)."""
+        assert buf4.dtype == self.torch.float32 and buf4.is_contiguous() and buf4.numel() == 4 * self.n_vertices
+        self._check(self.lib.sllbm_step_moments(self.h, _ptr(buf4)))
 
     def moments(self, sums=True):
         rho, u, v, T = (self._vertex_tensor(self.torch.float32) for _ in range(4))

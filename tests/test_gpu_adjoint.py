@@ -21,10 +21,12 @@ def _rel(a, b):
 def _small_cases():
     return {"svi_mapped": H.small_workloads()["svi"],
             "tgv_uniform": W.tgv256().resized(6, 5),
-            "sod_uniform": H.small_workloads()["sod"]}
+            "sod_uniform": H.small_workloads()["sod"],
+            # several 32 x 32 tiles of the one-pass S^T with ragged edges, clamped on both axes
+            "riemann_uniform": W.riemann_paper().resized(14, 12, keep_tau=True)}
 
 
-@pytest.mark.parametrize("name", ["svi_mapped", "tgv_uniform", "sod_uniform"])
+@pytest.mark.parametrize("name", ["svi_mapped", "tgv_uniform", "sod_uniform", "riemann_uniform"])
 def test_adjoint_step_matches_oracle(gpu_lib, name):
     from paper_1910_13918_gb300.sllbm import SLLBM
     w = _small_cases()[name]

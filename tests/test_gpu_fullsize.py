@@ -63,6 +63,45 @@ def test_long_run_f32_against_f64(gpu_lib, name, nsteps):
     assert abs(ma["mass"] / mb["mass"] - 1) < 1e-6
 
 
+def test_riemann_table3_to_end_time_f32_against_f64(gpu_lib):
+    """The 1024 x 1024-cell p = 3 grid with the Table III states to t = 0.3 (7447 steps), FP32
+    against FP64, the FP64 mass and energy taken every 100 steps.  Over the whole field the FP32
+    run follows the FP64 one to 1e-4 (L1, and at 99.9 % of the vertices); the largest pointwise
+    differences, a few 1e-3, sit on the shock fronts, where the two runs place a discontinuity a
+    fraction of a spacing apart.  The mass grows by what the zero-gradient boundaries let in
+    (density 1 at speed 0.7276 through half of the left and half of the bottom edge)."""
+    w = W.riemann_paper()
+    runs = {}
+    for prec in ("f32", "f64"):
+        s = _gpu(w, 0, prec)
+        log = []
+        done = 0
+        while done < w.steps:
+            n = min(100, w.steps - done)
+            s.step(n)
+            done += n
+            m = s.moments()
+            log.append((done, m["mass"], m["energy"]))
+        runs[prec] = (torch.stack([m[k].double() for k in ("rho", "u", "v", "T")]), log)
+        s.close()
+        torch.cuda.empty_cache()
+    a, b = runs["f32"][0], runs["f64"][0]
+    d = (a - b).abs()
+    umax = max(float(b[1].abs().max()), float(b[2].abs().max()))
+    scale = [b[0].abs(), umax, umax, b[3].abs()]
+    for i, name in enumerate(("rho", "u", "v", "T")):
+        l1 = float(d[i].sum() / (b[i].abs().sum() if i in (0, 3) else umax * b[i].numel()))
+        rel = (d[i] / scale[i]).reshape(-1)
+        p999 = float(torch.quantile(rel[::97], 0.999))
+        print(f"riemann t = 0.3 {name}: L1 {l1:.2e}, 99.9 % {p999:.2e}, max {float(rel.max()):.2e}")
+        assert l1 <= 1e-4 and p999 <= 1e-4, (name, l1, p999)
+    for (n, m32, e32), (_, m64, e64) in zip(runs["f32"][1], runs["f64"][1]):
+        assert abs(m32 / m64 - 1) < 2e-6 and abs(e32 / e64 - 1) < 2e-6, (n, m32, m64, e32, e64)
+    m0 = 0.25 * sum(st[0] for st in W.RIEMANN_STATES_PAPER.values())
+    t = w.steps * w.dt
+    assert abs(runs["f64"][1][-1][1] / (m0 + 0.7276 * t) - 1) < 0.01, (runs["f64"][1][-1], m0, t)
+
+
 def test_sod_long_run_f32_mass_tracks_f64(gpu_lib):
     """2000 steps of the Sod workload: the FP32 run keeps the FP64 run's mass (the interpolation
     reproduces constants exactly, so uniform regions do not drift) and its fields."""
@@ -156,4 +195,6 @@ def test_svi_adjoint_against_central_differences(gpu_lib):
     scale = max(ads)
     print("svi adjoint: max |AD| =", scale, "max |FD - AD| =", max(errs))
     assert scale > 1e-7, scale                      # a gradient well above FD round-off (~1e-9)
-    assert max(errs) <= 1e-3 * scale, (max(errs), scale)
+    # every direction within 1e-4 of the gradient's scale (the FP32 adjoint's rounding)
+    for d, (e, ad) in enumerate(zip(errs, ads)):
+        assert e <= 1e-4 * scale, (d, e, ad, scale)
