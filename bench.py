@@ -7,7 +7,9 @@ the fix-up launch for the vertices next to the boundaries.  The state (2 x 1.89 
 larger than the 129 MB L2, so no flush is needed between steps.  Beside it the same line
 carries the BF16-storage and plain FP64 forms of the step on the same grid, each with its error
 against the FP64 oracle after one step (sampled vertices) and against the FP64 GPU step after
-the whole run, and the 1024x1024-vertex Taylor-Green vortex at p = 4 as a second grid.
+the whole run, the 1024x1024-vertex Taylor-Green vortex at p = 4 as a second grid, and the 3D
+extension (D3Q125, the fused FP32 and the plain FP64 step) on the 128^3-vertex 3D Taylor-Green
+vortex.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--repeats R] [--impl ours|reference]
                     [--workload riemann_paper|tgv256|riemann|sod|svi|tgv16] [--quick]
@@ -485,6 +487,61 @@ def measure_grid(w, args, stream, ws, peak, sampler=None, precs=("f64", "f32", "
     return verts, res, out
 
 
+def measure_3d(args, stream, ws, peak):
+    """The 3D extension (D3Q125, hexahedral cells) on the 3D Taylor-Green vortex: the plain FP64
+    step and the fused FP32 step, W warm-up steps and R timed regions of K steps each, and the
+    FP32 fields against the FP64 ones after the same run."""
+    import numpy as np
+    import torch
+    from paper_1910_13918_gb300 import workloads as W
+    from paper_1910_13918_gb300.sllbm import SLLBM3D, BC_PERIODIC
+    w = W.tgv3d()
+    out, finals = {"workload": f"{w.name}: {w.shape[2]}^3 vertices ({w.cells[0]}^3 cells, p={w.order}), "
+                               f"D3Q125, f and g, dt={w.dt:.6g}, tau={w.tau:.6g}",
+                   "n_vertices": w.n_vertices, "updates_per_step": w.updates_per_step}, {}
+    for prec in ("f64", "f32"):
+        with torch.cuda.stream(stream):
+            s = SLLBM3D(cells=w.cells, order=w.order, box=w.box, bc=(BC_PERIODIC,) * 3, dt=w.dt,
+                        tau=w.tau, cv=w.cv, prec=prec, stream=stream)
+            s.precompute()
+            X, Y, Z = (t.cpu().numpy() for t in s.coords())
+            s.init(*w.fields(X, Y, Z))
+            del X, Y, Z
+            s.step(args.warmup)
+            ms = []
+            for _ in range(args.repeats):
+                e0, e1 = _event_pair()
+                _barrier()
+                torch.cuda.synchronize()
+                e0.record(stream)
+                s.step(args.steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                _barrier()
+                ms.append(max_over_ranks(e0.elapsed_time(e1)))
+            m = s.moments()
+            finals[prec] = torch.stack([m[k] for k in ("rho", "u", "v", "w", "T")])
+            s.close()
+            torch.cuda.empty_cache()
+        ms_step = statistics.median(ms) / args.steps
+        bpu = 16.0 if prec == "f64" else 8.0
+        achieved = w.updates_per_step * bpu / (ms_step * 1e-3) / 1e9
+        out[prec] = {"ms_per_step": ms_step, "value": w.updates_per_step * ws / (ms_step * 1e-3) / 1e9,
+                     "unit": UNIT, "kernel": "step3d_" + prec, "ms_per_region_repeats": ms,
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak, "bytes_per_update": bpu}}
+    a, b = finals["f32"].double(), finals["f64"].double()
+    umax = max(float(b[1].abs().max()), float(b[2].abs().max()), float(b[3].abs().max()), 1e-12)
+    d = (a - b).abs()
+    out["f32"]["err_vs_f64_gpu"] = {
+        "steps": args.warmup + args.repeats * args.steps,
+        "max_rel": {"rho": float((d[0] / b[0].abs()).max()), "u": float(d[1].max()) / umax,
+                    "v": float(d[2].max()) / umax, "w": float(d[3].max()) / umax,
+                    "T": float((d[4] / b[4].abs()).max())}}
+    out["speedup_f32_over_f64"] = out["f64"]["ms_per_step"] / out["f32"]["ms_per_step"]
+    return out
+
+
 def adjoint_time(s, stream, ws, updates):
     """20 adjoint steps (S^T J_C^T) at the moments of the context's current state."""
     import torch
@@ -572,6 +629,8 @@ def run_ours(args):
         one_step2 = {prec: res2[prec]["one_step"] for prec in precs}
         del res2
 
+    three_d = None if (args.quick or args.no_3d) else measure_3d(args, stream, ws, peak)
+
     if rank == 0:
         alg_bytes = updates * bytes_per_update(w, "f32", head["info"]["kernel"])
         achieved = alg_bytes / (ms_step * 1e-3) / 1e9
@@ -599,6 +658,7 @@ def run_ours(args):
             "gpu_launches_note": "per timed region of the headline (each of the repeats)",
             "mass_after": head["info"]["mass_after"],
             "secondary": secondary,
+            "d3q125": three_d,
         }
         if ws == 1 and not args.no_cpu_baseline:
             # the CPU leg: oracle timings, and the oracle's one-step values at the sampled
@@ -633,6 +693,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-3d", action="store_true", help="skip the 3D (D3Q125) entry")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -221,8 +221,10 @@ sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, int ny, doubl
  * 3D extension (the step the paper names as its next one): D3Q125, the tensor product of D1Q5
  * three times, on a uniform grid of hexahedral Lagrange cells of order 1..4 (Sec. II.E per axis),
  * with the same fourth-order equilibrium (Sec. II.A over index tuples in {x, y, z}^n), g^eq =
- * (2 C_v - 3) theta f^eq (Sec. II.D) and BGK (Eq. streaming_fg, Pr = 1).  Plain FP64 step on
- * full populations: params.velset = SLLBM_VEL_D3Q125, params.prec = SLLBM_PREC_F64_PLAIN,
+ * (2 C_v - 3) theta f^eq (Sec. II.D) and BGK (Eq. streaming_fg, Pr = 1).  params.velset =
+ * SLLBM_VEL_D3Q125 with params.prec = SLLBM_PREC_F64_PLAIN (plain FP64 step on full populations)
+ * or SLLBM_PREC_F32 (fused FP32 step: one launch per step, the state kept as FP32 deviations
+ * (f - w, g - K w) side by side; get_state / set_state still exchange FP64 full populations);
  * pr 0 or 1, cv >= 3/2 (cv = 3/2 carries f only; isothermal = 1 needs it).  Population field
  * [n_pop][125][nz][ny][nx], velocity i = 25a + 5b + c (D1Q5 indices of the x, y, z components in
  * Table I order); vertex arrays [nz][ny][nx].  Conventions otherwise as above.

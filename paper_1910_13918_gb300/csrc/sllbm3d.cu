@@ -43,11 +43,27 @@ struct Step3Args {
 struct Field3Args {
   const double *rho, *u, *v, *w, *T;     // init inputs
   double *orho, *ou, *ov, *ow, *oT;      // moment outputs
-  double* state;
+  double* state;                         // FP64: full populations [npop][125][nv]
+  float2* state32;                       // FP32: (f - w, g - K w) pairs [125][nv] (else null)
   long long nv;
   Consts cs;
   double K, cv;
   int npop;
+  int* flag;
+};
+
+// FP32 step: deviations from the lattice weights, f and g of a (velocity, vertex) side by side.
+struct Step3F32Args {
+  const float2* src;
+  float2* dst;
+  int nx, ny, nz;
+  long long nv;
+  int px, py, pz;
+  const int *offx, *offy, *offz;         // [5][n]
+  const float *wx, *wy, *wz;             // [5][n][p+1]
+  Consts cs;
+  float omega, K, cv, inv2cv;
+  int npop, iso;
   int* flag;
 };
 
@@ -149,6 +165,196 @@ __global__ void __launch_bounds__(128) step3d_f64_kernel(const __grid_constant__
   if (!(rho > 0.0 && theta > 0.0 && isfinite(rho) && isfinite(theta))) atomicOr(a.flag, 1);
 }
 
+// Index j of an axis of n vertices, wrapped once on periodic axes: stencil nodes lie within one
+// period of the vertex (the departure displacement is far below the domain length).
+__device__ __forceinline__ int wrap1(int j, int n, int periodic) {
+  if (!periodic) return j;
+  return j < 0 ? j + n : (j >= n ? j - n : j);
+}
+
+// Weight w_abc of velocity i = 25a + 5b + c (FP32).
+__device__ __forceinline__ float w3f(const Consts& cs, int i) {
+  return cs.wf[i / 25] * cs.wf[(i / 5) % 5] * cs.wf[i % 5];
+}
+
+// Fused FP32 step, one thread per vertex, one launch.  First sweep: every velocity's (f, g) pair
+// is interpolated at its departure point (tensor product of the three 1D Lagrange bases, each in
+// the difference form v_0 + sum_{k>=1} w_k (v_k - v_0), which keeps constant fields exact) and
+// written to the destination, and its moments are summed.  Second sweep: the thread reads its
+// own 125 pairs back (from L1/L2: no second pass over HBM), relaxes them toward the factorised
+// equilibrium and sums the residual moments of (f^eq - f); the residuals (the FP32 rounding of
+// the equilibrium) are then removed at the rest velocity and at (s, 0, 0), (0, s, 0), (0, 0, s)
+// for mass and momentum, and on g at the rest velocity for the energy.
+template <int P>
+__global__ void __launch_bounds__(128) step3d_f32_kernel(const __grid_constant__ Step3F32Args a) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= a.nv) return;
+  const int ix = (int)(v % a.nx);
+  const long long t = v / a.nx;
+  const int iy = (int)(t % a.ny), iz = (int)(t / a.ny);
+  const size_t plane = (size_t)a.nv;
+  float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, a2 = 0.f, G = 0.f;
+#pragma unroll 1
+  for (int i = 0; i < kQ3; ++i) {
+    const int ia = i / 25, ib = (i / 5) % 5, ic = i % 5;
+    const int sx = ix + a.offx[ia * a.nx + ix], sy = iy + a.offy[ib * a.ny + iy],
+              sz = iz + a.offz[ic * a.nz + iz];
+    const float* wx = a.wx + (size_t)(ia * a.nx + ix) * (P + 1);
+    const float* wy = a.wy + (size_t)(ib * a.ny + iy) * (P + 1);
+    const float* wz = a.wz + (size_t)(ic * a.nz + iz) * (P + 1);
+    const float2* pl = a.src + (size_t)i * plane;
+    int cx[P + 1], cy[P + 1], cz[P + 1];
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      cx[k] = wrap1(sx + k, a.nx, a.px);
+      cy[k] = wrap1(sy + k, a.ny, a.py);
+      cz[k] = wrap1(sz + k, a.nz, a.pz);
+    }
+    float2 zs[P + 1];
+#pragma unroll
+    for (int kc = 0; kc <= P; ++kc) {
+      const size_t zoff = (size_t)cz[kc] * a.ny;
+      float2 ys[P + 1];
+#pragma unroll
+      for (int kb = 0; kb <= P; ++kb) {
+        const float2* row = pl + (zoff + (size_t)cy[kb]) * a.nx;
+        const float2 b0 = __ldg(row + cx[0]);
+        float2 acc = b0;
+#pragma unroll
+        for (int ka = 1; ka <= P; ++ka) acc = fma2(bcast2(__ldg(wx + ka)), sub2(__ldg(row + cx[ka]), b0), acc);
+        ys[kb] = acc;
+      }
+      float2 acc = ys[0];
+#pragma unroll
+      for (int kb = 1; kb <= P; ++kb) acc = fma2(bcast2(__ldg(wy + kb)), sub2(ys[kb], ys[0]), acc);
+      zs[kc] = acc;
+    }
+    float2 acc = zs[0];
+#pragma unroll
+    for (int kc = 1; kc <= P; ++kc) acc = fma2(bcast2(__ldg(wz + kc)), sub2(zs[kc], zs[0]), acc);
+    a.dst[(size_t)i * plane + v] = acc;
+    const float ex = a.cs.xif[ia], ey = a.cs.xif[ib], ez = a.cs.xif[ic];
+    drho += acc.x;
+    jx += ex * acc.x;
+    jy += ey * acc.x;
+    jz += ez * acc.x;
+    a2 += (ex * ex + ey * ey + ez * ez) * acc.x;
+    G += acc.y;
+  }
+  if (a.npop != 2) G = 0.f;
+  const float rho = 1.f + drho, inv_rho = __frcp_rn(rho);
+  const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+  // theta - 1 = (A2 + G - rho |u|^2 - 2 C_v drho) / (2 C_v rho)   (sum w |xi|^2 + K = 2 C_v)
+  const float qk = (a2 + G - rho * (ux * ux + uy * uy + uz * uz) - 2.f * a.cv * drho) * inv_rho * a.inv2cv;
+  const float q = a.iso ? 0.f : qk;
+  // per-axis factors X_k(a) = A_k(u_x) he_k(a), Y_l(b) likewise, Zc_n(c) = sum_{m <= n} A_m(u_z)
+  // he_m(c): 1 + S_abc = sum_{k + l + m <= 4} X_k(a) Y_l(b) Z_m(c), and f^eq - w = w (drho + rho S)
+  float Ax[5], Ay[5], Az[5];
+  {
+    const float u3[3] = {ux, uy, uz};
+    float* A3[3] = {Ax, Ay, Az};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float u = u3[d];
+      A3[d][0] = 1.f;
+      A3[d][1] = u;
+      A3[d][2] = u * u + q;
+      A3[d][3] = u * (u * u + 3.f * q);
+      A3[d][4] = u * u * (u * u + 6.f * q) + 3.f * q * q;
+    }
+  }
+  float Zc[5][5];   // [n][c], compile-time indices only
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      acc += Az[m] * a.cs.hef[m][c];
+      Zc[m][c] = acc;
+    }
+  }
+  const float om = a.omega, Kq1 = a.K * (1.f + q), Kq = a.K * q;
+  const float2 om2 = bcast2(om);
+  float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, re = 0.f;
+#pragma unroll 1
+  for (int ia = 0; ia < kQ1; ++ia) {
+    float Xa[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Xa[k] = Ax[k] * a.cs.hef[k][ia];
+    const float ex = a.cs.xif[ia], wa = a.cs.wf[ia];
+#pragma unroll 1
+    for (int ib = 0; ib < kQ1; ++ib) {
+      float Yb[5];
+#pragma unroll
+      for (int l = 0; l < 5; ++l) Yb[l] = Ay[l] * a.cs.hef[l][ib];
+      const float ey = a.cs.xif[ib], wab = wa * a.cs.wf[ib];
+#pragma unroll
+      for (int ic = 0; ic < kQ1; ++ic) {
+        const int i = 25 * ia + 5 * ib + ic;
+        float s1 = 0.f;
+#pragma unroll
+        for (int k = 0; k <= 4; ++k) {
+          float sl = 0.f;
+#pragma unroll
+          for (int l = 0; l <= 4 - k; ++l) sl += Yb[l] * Zc[4 - k - l][ic];
+          s1 += Xa[k] * sl;
+        }
+        const float w = wab * a.cs.wf[ic];
+        const float ef = w * (drho + rho * (s1 - 1.f));
+        const float eg = Kq1 * ef + Kq * w;   // g^eq - K w = K ((1 + q)(f^eq - w) + q w)
+        float2* o = a.dst + (size_t)i * plane + v;
+        const float2 fg = *o;
+        const float2 d = sub2(make_float2(ef, a.npop == 2 ? eg : 0.f), fg);
+        const float ez = a.cs.xif[ic];
+        r0 += d.x;
+        r1 += ex * d.x;
+        r2 += ey * d.x;
+        r3 += ez * d.x;
+        re += (ex * ex + ey * ey + ez * ez) * d.x + d.y;
+        *o = fma2(om2, d, fg);
+      }
+    }
+  }
+  {   // remove the residuals (see above): i = 25 a + 5 b + c; s = xi of index 1
+    const float inv_s = a.cs.inv_xi1f, s2 = a.cs.xi1sqf;
+    const float d1 = r1 * inv_s, d2 = r2 * inv_s, d3 = r3 * inv_s;
+    const float d0 = r0 - d1 - d2 - d3;
+    const float de = re - s2 * (d1 + d2 + d3);
+    float2* o = a.dst + v;
+    o[0].x -= om * d0;
+    o[25 * plane].x -= om * d1;
+    o[5 * plane].x -= om * d2;
+    o[1 * plane].x -= om * d3;
+    if (a.npop == 2) {
+      o[0].y -= om * de;
+    } else if (!a.iso) {   // one population: energy along (+-s, 0, 0) and -2 at rest
+      const float e = om * 0.5f * de * inv_s * inv_s;
+      o[25 * plane].x -= e;
+      o[75 * plane].x -= e;
+      o[0].x += 2.f * e;
+    }
+  }
+  if (!((rho > 0.f) && (qk > -1.f) && isfinite(rho) && isfinite(qk))) atomicOr(a.flag, 1);
+}
+
+// FP32 pairs <-> dense FP64 full populations [npop][125][nv].
+__global__ void convert3d_kernel(float2* pairs, double* dense, long long nv, int npop, double K,
+                                 Consts cs, int to_dense) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)kQ3 * nv) return;
+  const int i = (int)(e / nv);
+  const double w = cs.w[i / 25] * cs.w[(i / 5) % 5] * cs.w[i % 5];
+  if (to_dense) {
+    const float2 p = pairs[e];
+    dense[e] = (double)p.x + w;
+    if (npop == 2) dense[(size_t)kQ3 * nv + e] = (double)p.y + K * w;
+  } else {
+    const float f = (float)(dense[e] - w);
+    const float g = npop == 2 ? (float)(dense[(size_t)kQ3 * nv + e] - K * w) : 0.f;
+    pairs[e] = make_float2(f, g);
+  }
+}
+
 __global__ void init3d_kernel(const __grid_constant__ Field3Args a) {
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= a.nv) return;
@@ -160,8 +366,14 @@ __global__ void init3d_kernel(const __grid_constant__ Field3Args a) {
   const size_t plane = (size_t)a.nv;
   for (int i = 0; i < kQ3; ++i) {
     const double feq = eq3(a.cs, rho, Ax, Ay, Az, i / 25, (i / 5) % 5, i % 5);
-    a.state[(size_t)i * plane + v] = feq;
-    if (a.npop == 2) a.state[(size_t)(kQ3 + i) * plane + v] = a.K * theta * feq;
+    if (a.state32) {
+      const double w = a.cs.w[i / 25] * a.cs.w[(i / 5) % 5] * a.cs.w[i % 5];
+      a.state32[(size_t)i * plane + v] =
+          make_float2((float)(feq - w), a.npop == 2 ? (float)(a.K * theta * feq - a.K * w) : 0.f);
+    } else {
+      a.state[(size_t)i * plane + v] = feq;
+      if (a.npop == 2) a.state[(size_t)(kQ3 + i) * plane + v] = a.K * theta * feq;
+    }
   }
 }
 
@@ -171,8 +383,16 @@ __global__ void moments3d_kernel(const __grid_constant__ Field3Args a) {
   const size_t plane = (size_t)a.nv;
   double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, e2 = 0.0;
   for (int i = 0; i < kQ3; ++i) {
-    const double f = a.state[(size_t)i * plane + v];
-    const double g = a.npop == 2 ? a.state[(size_t)(kQ3 + i) * plane + v] : 0.0;
+    double f, g;
+    if (a.state32) {
+      const float2 p = a.state32[(size_t)i * plane + v];
+      const double w = a.cs.w[i / 25] * a.cs.w[(i / 5) % 5] * a.cs.w[i % 5];
+      f = (double)p.x + w;
+      g = a.npop == 2 ? (double)p.y + a.K * w : 0.0;
+    } else {
+      f = a.state[(size_t)i * plane + v];
+      g = a.npop == 2 ? a.state[(size_t)(kQ3 + i) * plane + v] : 0.0;
+    }
     const double cx = a.cs.xi[i / 25], cy = a.cs.xi[(i / 5) % 5], cz = a.cs.xi[i % 5];
     rho += f;
     jx += f * cx;
@@ -224,6 +444,8 @@ void d1q5_consts(Consts& cs) {
     cs.wf[a] = (float)w[a];
     for (int k = 0; k < kQ1; ++k) cs.hef[k][a] = (float)cs.he[k][a];
   }
+  cs.inv_xi1f = (float)(1.0 / xi[1]);
+  cs.xi1sqf = (float)(xi[1] * xi[1]);
 }
 
 void axis3(AxisK& ax, int n_cells, int p, double lo, double hi, int periodic, int nodes) {
@@ -250,8 +472,9 @@ struct sllbm3d_ctx {
   AxisK ax{}, ay{}, az{};
   Consts cs{};
   int npop = 2;
+  bool f32 = false;                      // FP32 deviation pairs (else FP64 full populations)
   long long nv = 0;
-  double* state[2] = {nullptr, nullptr};
+  double* state[2] = {nullptr, nullptr}; // FP32: reinterpreted as float2 [125][nv]
   int cur = 0;
   bool precomputed = false, initialized = false;
   int* off[3] = {nullptr, nullptr, nullptr};
@@ -289,7 +512,11 @@ sllbm_status alloc3(sllbm3d_ctx* c, T** ptr, size_t count) {
 
 unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-size_t state_doubles(const sllbm3d_ctx* c) { return (size_t)c->npop * kQ3 * c->nv; }
+// storage of one state buffer in 8-byte units: FP64 populations or FP32 (f, g) pairs
+size_t state_doubles(const sllbm3d_ctx* c) { return (size_t)(c->f32 ? 1 : c->npop) * kQ3 * c->nv; }
+// doubles of the dense FP64 layout exchanged by get_state / set_state
+size_t dense_doubles(const sllbm3d_ctx* c) { return (size_t)c->npop * kQ3 * c->nv; }
+float2* pairs(const sllbm3d_ctx* c, int k) { return reinterpret_cast<float2*>(c->state[k]); }
 
 }  // namespace
 
@@ -299,7 +526,8 @@ sllbm_status sllbm3d_create(const sllbm_grid3_desc* g, const sllbm_params* p, vo
   if (!g || !p || !out) return SLLBM_ERR_ARG;
   *out = nullptr;
   if (g->order < 1 || g->order > 4) return SLLBM_ERR_UNSUPPORTED;
-  if (p->velset != SLLBM_VEL_D3Q125 || p->prec != SLLBM_PREC_F64_PLAIN) return SLLBM_ERR_UNSUPPORTED;
+  if (p->velset != SLLBM_VEL_D3Q125 || (p->prec != SLLBM_PREC_F64_PLAIN && p->prec != SLLBM_PREC_F32))
+    return SLLBM_ERR_UNSUPPORTED;
   if (p->pr != 0.0 && p->pr != 1.0) return SLLBM_ERR_UNSUPPORTED;
   if (g->nx_cells < 1 || g->ny_cells < 1 || g->nz_cells < 1 || !(g->x1 > g->x0) || !(g->y1 > g->y0) ||
       !(g->z1 > g->z0))
@@ -324,6 +552,7 @@ sllbm_status sllbm3d_create(const sllbm_grid3_desc* g, const sllbm_params* p, vo
   axis3(c->az, g->nz_cells, g->order, g->z0, g->z1, g->bc_z == SLLBM_BC_PERIODIC, g->nodes);
   c->nv = (long long)c->ax.nv * c->ay.nv * c->az.nv;
   c->npop = p->cv == 1.5 ? 1 : 2;
+  c->f32 = p->prec == SLLBM_PREC_F32;
   sllbm_status s = SLLBM_OK;
   for (int k = 0; k < 2 && s == SLLBM_OK; ++k) s = alloc3(c, &c->state[k], state_doubles(c));
   if (s == SLLBM_OK) s = alloc3(c, &c->flag, 1);
@@ -389,6 +618,7 @@ sllbm_status sllbm3d_init_equilibrium(sllbm3d_ctx* c, const double* rho, const d
   a.w = w;
   a.T = T;
   a.state = c->state[c->cur];
+  a.state32 = c->f32 ? pairs(c, c->cur) : nullptr;
   a.nv = c->nv;
   a.cs = c->cs;
   a.K = 2.0 * c->p.cv - 3.0;
@@ -425,6 +655,44 @@ sllbm_status sllbm3d_step(sllbm3d_ctx* c, int nsteps) {
   a.iso = c->p.isothermal;
   a.flag = c->flag;
   const unsigned blocks = blocks_for(c->nv, 128);
+  if (c->f32) {
+    Step3F32Args b{};
+    b.nx = a.nx;
+    b.ny = a.ny;
+    b.nz = a.nz;
+    b.nv = a.nv;
+    b.px = a.px;
+    b.py = a.py;
+    b.pz = a.pz;
+    b.offx = a.offx;
+    b.offy = a.offy;
+    b.offz = a.offz;
+    b.wx = c->w32[0];
+    b.wy = c->w32[1];
+    b.wz = c->w32[2];
+    b.cs = c->cs;
+    b.omega = (float)a.omega;
+    b.K = (float)a.K;
+    b.cv = (float)a.cv;
+    b.inv2cv = (float)(0.5 / a.cv);
+    b.npop = a.npop;
+    b.iso = a.iso;
+    b.flag = a.flag;
+    for (int k = 0; k < nsteps; ++k) {
+      b.src = pairs(c, c->cur);
+      b.dst = pairs(c, c->cur ^ 1);
+      switch (c->g.order) {
+        case 1: step3d_f32_kernel<1><<<blocks, 128, 0, c->stream>>>(b); break;
+        case 2: step3d_f32_kernel<2><<<blocks, 128, 0, c->stream>>>(b); break;
+        case 3: step3d_f32_kernel<3><<<blocks, 128, 0, c->stream>>>(b); break;
+        default: step3d_f32_kernel<4><<<blocks, 128, 0, c->stream>>>(b); break;
+      }
+      const sllbm_status s = cuda3(c, cudaGetLastError(), "step3d_f32_kernel");
+      if (s != SLLBM_OK) return s;
+      c->cur ^= 1;
+    }
+    return SLLBM_OK;
+  }
   for (int k = 0; k < nsteps; ++k) {
     a.src = c->state[c->cur];
     a.dst = c->state[c->cur ^ 1];
@@ -451,8 +719,10 @@ sllbm_status sllbm3d_moments(sllbm3d_ctx* c, double* rho, double* u, double* v, 
   a.ow = w;
   a.oT = T;
   a.state = c->state[c->cur];
+  a.state32 = c->f32 ? pairs(c, c->cur) : nullptr;
   a.nv = c->nv;
   a.cs = c->cs;
+  a.K = 2.0 * c->p.cv - 3.0;
   a.cv = c->p.cv;
   a.npop = c->npop;
   a.flag = c->flag;
@@ -468,12 +738,24 @@ sllbm_status sllbm3d_moments(sllbm3d_ctx* c, double* rho, double* u, double* v, 
 
 sllbm_status sllbm3d_get_state(sllbm3d_ctx* c, double* dst) {
   if (!c || !dst) return fail3(c, SLLBM_ERR_ARG, "null pointer");
+  if (c->f32) {
+    convert3d_kernel<<<blocks_for((long long)kQ3 * c->nv, 256), 256, 0, c->stream>>>(
+        pairs(c, c->cur), dst, c->nv, c->npop, 2.0 * c->p.cv - 3.0, c->cs, 1);
+    return cuda3(c, cudaGetLastError(), "convert3d_kernel");
+  }
   return cuda3(c, cudaMemcpyAsync(dst, c->state[c->cur], state_doubles(c) * sizeof(double), cudaMemcpyDeviceToDevice,
                                   c->stream), "cudaMemcpyAsync");
 }
 
 sllbm_status sllbm3d_set_state(sllbm3d_ctx* c, const double* src) {
   if (!c || !src) return fail3(c, SLLBM_ERR_ARG, "null pointer");
+  if (c->f32) {
+    convert3d_kernel<<<blocks_for((long long)kQ3 * c->nv, 256), 256, 0, c->stream>>>(
+        pairs(c, c->cur), const_cast<double*>(src), c->nv, c->npop, 2.0 * c->p.cv - 3.0, c->cs, 0);
+    const sllbm_status s = cuda3(c, cudaGetLastError(), "convert3d_kernel");
+    if (s == SLLBM_OK) c->initialized = true;
+    return s;
+  }
   const sllbm_status s = cuda3(c, cudaMemcpyAsync(c->state[c->cur], src, state_doubles(c) * sizeof(double),
                                                   cudaMemcpyDeviceToDevice, c->stream), "cudaMemcpyAsync");
   if (s == SLLBM_OK) c->initialized = true;

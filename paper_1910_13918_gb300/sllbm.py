@@ -287,10 +287,11 @@ class SLLBM:
 
 
 class SLLBM3D:
-    """The 3D extension (D3Q125, hexahedral cells, plain FP64 step) on the current CUDA device."""
+    """The 3D extension (D3Q125, hexahedral cells) on the current CUDA device: the plain FP64 step
+    (``prec="f64"``) or the fused FP32 step on deviation pairs (``prec="f32"``)."""
 
     def __init__(self, *, cells, order, box, bc, dt, tau, cv, isothermal=False,
-                 nodes=NODES_GLC, stream=None):
+                 nodes=NODES_GLC, prec="f64", stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("SLLBM3D needs a CUDA device; there is no CPU path")
@@ -298,7 +299,10 @@ class SLLBM3D:
         self.lib = load()
         (x0, x1), (y0, y1), (z0, z1) = box
         g = GridDesc3(*cells, order, x0, x1, y0, y1, z0, z1, *bc, nodes)
-        p = Params(VEL_D3Q125, dt, tau, cv, 1.0, PREC_F64_PLAIN, 1.0, int(bool(isothermal)))
+        if prec not in ("f32", "f64"):
+            raise ValueError("3D precisions: f32 (fused FP32 step) or f64 (plain FP64 step)")
+        self.prec = prec
+        p = Params(VEL_D3Q125, dt, tau, cv, 1.0, PRECISIONS[prec], 1.0, int(bool(isothermal)))
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         st = self.lib.sllbm3d_create(ctypes.byref(g), ctypes.byref(p),

@@ -407,6 +407,67 @@ def sdp(points=16, step_factor=1):
                     dt, nu / dt + 0.5, steps, "sdp", seed=7, extra={"U": U, "t_end": t_end})
 
 
+# ---------------------------------------------------------------------------------------------
+# 3D (the extension the paper names as its next step: D3Q125 on hexahedral cells)
+# ---------------------------------------------------------------------------------------------
+C_MAX_3D = math.sqrt(3.0 * (5.0 + math.sqrt(10.0)))   # largest D3Q125 speed, 4.9487
+
+
+@dataclasses.dataclass
+class Workload3:
+    name: str
+    cells: tuple
+    order: int
+    box: tuple                     # ((x0, x1), (y0, y1), (z0, z1))
+    periodic: bool
+    dt: float
+    tau: float
+    steps: int
+    cv: float = CV
+    extra: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def shape(self):               # (nz, ny, nx) vertices
+        n = [c * self.order + (0 if self.periodic else 1) for c in self.cells]
+        return (n[2], n[1], n[0])
+
+    @property
+    def n_vertices(self):
+        nz, ny, nx = self.shape
+        return nx * ny * nz
+
+    @property
+    def n_populations(self):
+        return 1 if self.cv == 1.5 else 2
+
+    @property
+    def updates_per_step(self):
+        return self.n_vertices * 125 * self.n_populations
+
+    def fields(self, x, y, z):
+        """The 3D Taylor-Green vortex: u = U0 sin x cos y cos z, v = -U0 cos x sin y cos z, w = 0,
+        p = 1 + (U0^2 / 16)(cos 2x + cos 2y)(cos 2z + 2), rho = 1, T = p / rho."""
+        U0 = self.extra["U0"]
+        x, y, z = (np.asarray(a, np.float64) for a in (x, y, z))
+        u = U0 * np.sin(x) * np.cos(y) * np.cos(z)
+        v = -U0 * np.cos(x) * np.sin(y) * np.cos(z)
+        w = np.zeros_like(x)
+        p = 1.0 + U0 ** 2 / 16.0 * (np.cos(2 * x) + np.cos(2 * y)) * (np.cos(2 * z) + 2.0)
+        return np.ones_like(x), u, v, w, p
+
+
+def tgv3d(cells=64, order=2, ma=0.1, re=1600.0, steps=100):
+    """3D Taylor-Green vortex on the periodic box [0, 2 pi]^3, cells^3 hexahedral cells of order
+    p: U0 = Ma c_s, nu = U0 / Re (unit length), dt from CFL 0.5 on the vertex spacing with
+    respect to the largest D3Q125 speed."""
+    L = 2.0 * math.pi
+    h = L / (cells * order)
+    dt = 0.5 * h / C_MAX_3D
+    nu = ma / re
+    return Workload3(f"tgv3d{cells}_p{order}", (cells, cells, cells), order, ((0.0, L),) * 3, True,
+                     dt, nu / dt + 0.5, steps, extra={"U0": ma})
+
+
 ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
        "riemann_paper": riemann_paper, "riemann_glc": riemann_nodes,
        "riemann_equidistant": lambda: riemann_nodes("equidistant"), "svi": svi, "svi_pr": svi_pr, "sdp": sdp,

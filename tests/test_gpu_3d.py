@@ -43,11 +43,11 @@ def _oracle(case):
     return o3.run(f, g, o3.Departures3(grid, dt), tau, cv, steps, isothermal=iso)
 
 
-def _gpu(case):
+def _gpu(case, prec="f64"):
     from paper_1910_13918_gb300.sllbm import SLLBM3D, BC_PERIODIC, BC_ZERO_GRADIENT
     cells, p, box, periodic, dt, tau, cv, iso, steps = case
     bc = (BC_PERIODIC if periodic else BC_ZERO_GRADIENT,) * 3
-    s = SLLBM3D(cells=cells, order=p, box=box, bc=bc, dt=dt, tau=tau, cv=cv, isothermal=iso)
+    s = SLLBM3D(cells=cells, order=p, box=box, bc=bc, dt=dt, tau=tau, cv=cv, isothermal=iso, prec=prec)
     s.precompute()
     X, Y, Z = (t.cpu().numpy() for t in s.coords())
     s.init(*_fields(X, Y, Z, box, 3))
@@ -84,3 +84,42 @@ def test_3d_state_round_trip(gpu_lib):
     s.set_state(st)
     s.step(1)
     assert np.array_equal(s.get_state().cpu().numpy(), after.cpu().numpy())
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_3d_fused_f32_step_against_oracle(gpu_lib, name):
+    """The fused FP32 step (deviation pairs, one launch a step): rho, u, v, w, T after the case's
+    steps within the FP32 tolerance of the 2D step (1e-5, velocities relative to the flow's
+    scale), and populations to FP32 precision of the deviations (3e-5 of their largest value)."""
+    case = CASES[name]
+    s = _gpu(case, "f32")
+    f, g = _oracle(case)
+    st = s.get_state().cpu().numpy()
+    xi, w = o3.d3q125()
+    scale = np.max(np.abs(f - w[:, None, None, None]))
+    # the deviations f - w are stored in FP32: a few units of their last place
+    assert np.max(np.abs(st[0] - f)) <= 3e-5 * scale, np.max(np.abs(st[0] - f)) / scale
+    m = s.moments()
+    rho, u, th = o3.macroscopic(f, g, case[6])
+    umax = max(float(np.max(np.abs(u))), 1e-3)
+    assert np.max(np.abs(m["rho"].cpu().numpy() / rho - 1)) < 1e-5
+    assert np.max(np.abs(m["T"].cpu().numpy() / th - 1)) < 1e-5
+    for k, name_ in enumerate(("u", "v", "w")):
+        assert np.max(np.abs(m[name_].cpu().numpy() - u[..., k])) < 1e-5 * umax, name_
+
+
+def test_3d_fused_f32_keeps_mass_and_energy_of_f64(gpu_lib):
+    """50 steps on the periodic case: the FP32 step's total mass and energy (sums of rho and
+    rho E over the vertices) follow the FP64 step's to FP32 rounding -- the residual correction
+    keeps the conserved moments of every collision -- while both carry the scheme's own small
+    interpolation loss."""
+    case = CASES["periodic_p2"]
+    tot = {}
+    for prec in ("f64", "f32"):
+        s = _gpu(case, prec)
+        s.step(50)
+        st = s.get_state().cpu().numpy()
+        g = st[1] if st.shape[0] == 2 else np.zeros_like(st[0])
+        tot[prec] = (float(st[0].sum()), float(o3.total_energy_density(st[0], g).sum()))
+    (m64, e64), (m32, e32) = tot["f64"], tot["f32"]
+    assert abs(m32 / m64 - 1) < 1e-6 and abs(e32 / e64 - 1) < 1e-6, (m32 / m64 - 1, e32 / e64 - 1)
