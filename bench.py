@@ -42,8 +42,12 @@ SECONDARY = "tgv256"          # second grid of the line: the Taylor-Green vortex
 # DRAM traffic (read + write bytes per launch) of the step kernel from an ncu capture, keyed by
 # (kernel source digest, workload, precision); reported as null once the kernel source changes.
 NCU_TRAFFIC = {
-    ("2bc27c161d73873e", "tgv256_p4", "f32"): 396.2e6,
-    ("2bc27c161d73873e", "svi512x256_p2_mapped", "f32"): 352.2e6,
+    # 512^2-cell capture: 526.3 MB read + 429.7 MB written for 2,362,369 vertices, scaled by the
+    # vertex count to the 3073^2 grid (a multi-pass capture of that grid exceeds the size rule)
+    ("e04b2b9fb294aa87", "riemann1024_p3_tableIII", "f32"): 956.04e6 * 9443329 / 2362369,
+    ("e04b2b9fb294aa87", "riemann512_p3_tableIII", "f32"): 956.04e6,
+    # full-size capture: 221.6 MB read + 174.7 MB written
+    ("e04b2b9fb294aa87", "tgv256_p4", "f32"): 396.3e6,
 }
 
 # Sources that decide what the fused kernels of NCU_TRAFFIC do and how they are launched on
@@ -461,7 +465,7 @@ def _summary(w, prec, r, args, ws, peak):
                          "bytes_per_update": bytes_per_update(w, prec, r["info"]["kernel"])}}
 
 
-def measure_grid(w, args, stream, ws, peak, sampler=None, precs=("f64", "f32", "bf16")):
+def measure_grid(w, args, stream, ws, peak, sampler=None, precs=("f64", "f32", "bf16"), keep="f32"):
     """FP64 plain, FP32 and BF16-storage forms on one grid: timings, the sampled one-step values
     and, for FP32 and BF16, the whole-field error against the FP64 GPU step after the same run."""
     import torch
@@ -469,7 +473,7 @@ def measure_grid(w, args, stream, ws, peak, sampler=None, precs=("f64", "f32", "
     res, out = {}, {}
     for prec in precs:
         res[prec] = measure(w, prec, args, stream, verts,
-                            sampler=sampler if prec == "f32" else None, keep=(prec == "f32"))
+                            sampler=sampler if prec == keep else None, keep=(prec == keep))
         out[prec] = _summary(w, prec, res[prec], args, ws, peak)
         torch.cuda.empty_cache()
     nsteps = 1 + args.warmup + args.repeats * args.steps
@@ -487,7 +491,7 @@ def measure_grid(w, args, stream, ws, peak, sampler=None, precs=("f64", "f32", "
     return verts, res, out
 
 
-def measure_3d(args, stream, ws, peak):
+def measure_3d(args, stream, ws, peak, precs=("f64", "f32")):
     """The 3D extension (D3Q125, hexahedral cells) on the 3D Taylor-Green vortex: the plain FP64
     step and the fused FP32 step, W warm-up steps and R timed regions of K steps each, and the
     FP32 fields against the FP64 ones after the same run."""
@@ -495,11 +499,11 @@ def measure_3d(args, stream, ws, peak):
     import torch
     from paper_1910_13918_gb300 import workloads as W
     from paper_1910_13918_gb300.sllbm import SLLBM3D, BC_PERIODIC
-    w = W.tgv3d()
+    w = W.tgv3d(cells=args.d3_cells)
     out, finals = {"workload": f"{w.name}: {w.shape[2]}^3 vertices ({w.cells[0]}^3 cells, p={w.order}), "
                                f"D3Q125, f and g, dt={w.dt:.6g}, tau={w.tau:.6g}",
                    "n_vertices": w.n_vertices, "updates_per_step": w.updates_per_step}, {}
-    for prec in ("f64", "f32"):
+    for prec in precs:
         with torch.cuda.stream(stream):
             s = SLLBM3D(cells=w.cells, order=w.order, box=w.box, bc=(BC_PERIODIC,) * 3, dt=w.dt,
                         tau=w.tau, cv=w.cv, prec=prec, stream=stream)
@@ -530,6 +534,8 @@ def measure_3d(args, stream, ws, peak):
                      "unit": UNIT, "kernel": "step3d_" + prec, "ms_per_region_repeats": ms,
                      "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                   "frac": achieved / peak, "bytes_per_update": bpu}}
+    if "f64" not in finals:
+        return out
     a, b = finals["f32"].double(), finals["f64"].double()
     umax = max(float(b[1].abs().max()), float(b[2].abs().max()), float(b[3].abs().max()), 1e-12)
     d = (a - b).abs()
@@ -593,6 +599,13 @@ def run_ours(args):
     import torch
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
+    if args.only_3d:   # the 3D entry alone (FP32 step only with --quick)
+        peaks, _ = _peaks()
+        out = measure_3d(args, torch.cuda.Stream(), ws, float(peaks.get("hbm_gbs", 6800.0)),
+                         ("f32",) if args.quick else ("f64", "f32"))
+        if rank == 0:
+            print(json.dumps({"d3q125": out}))
+        return 0
     dist = None
     if ws > 1:
         import torch.distributed as dist
@@ -602,9 +615,10 @@ def run_ours(args):
     w = _workload(args.workload)
     stream = torch.cuda.Stream()
     sampler = ClockSampler(local)
-    precs = ("f32",) if args.quick else ("f64", "f32", "bf16")
-    verts, res, forms = measure_grid(w, args, stream, ws, peak, sampler, precs)
-    head = res["f32"]
+    hp = args.prec if args.quick else "f32"   # precision of the headline form
+    precs = (hp,) if args.quick else ("f64", "f32", "bf16")
+    verts, res, forms = measure_grid(w, args, stream, ws, peak, sampler, precs, keep=hp)
+    head = res[hp]
     s = head["ctx"]
     ms_med = statistics.median(head["ms"])
     ms_step = ms_med / args.steps
@@ -614,7 +628,7 @@ def run_ours(args):
     adjoint = None
     if not args.no_adjoint and not w.isothermal and w.pr == 1.0:
         adjoint = adjoint_time(s, stream, ws, updates)
-        adjoint["launches_per_step"] = 2 if w.map_a else 3
+        adjoint["launches_per_step"] = 2
     e2e = None if args.no_e2e else e2e_time(s, args, ws, updates)
     s.close()
     torch.cuda.empty_cache()
@@ -632,13 +646,13 @@ def run_ours(args):
     three_d = None if (args.quick or args.no_3d) else measure_3d(args, stream, ws, peak)
 
     if rank == 0:
-        alg_bytes = updates * bytes_per_update(w, "f32", head["info"]["kernel"])
+        alg_bytes = updates * bytes_per_update(w, hp, head["info"]["kernel"])
         achieved = alg_bytes / (ms_step * 1e-3) / 1e9
-        traffic = NCU_TRAFFIC.get((_kernel_digest(), w.name, "f32"))
+        traffic = NCU_TRAFFIC.get((_kernel_digest(), w.name, hp))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": hp, "data": "synthetic",
             "config": {"workload": _workload_desc(w), "kernel": head["info"]["kernel"],
                        "n_vertices": w.n_vertices, "updates_per_step": updates,
                        "l2": "state 2 x %.0f MB > 129 MB L2, no flush" % (head["info"]["state_bytes"] / 1e6),
@@ -689,11 +703,15 @@ def main():
     ap.add_argument("--repeats", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="riemann_paper")
-    ap.add_argument("--quick", action="store_true", help="FP32 headline only: no other forms or grid")
+    ap.add_argument("--quick", action="store_true", help="one form (--prec) of the headline grid only")
+    ap.add_argument("--prec", default="f32", choices=["f32", "bf16", "f64"],
+                    help="the form timed with --quick")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-3d", action="store_true", help="skip the 3D (D3Q125) entry")
+    ap.add_argument("--only-3d", action="store_true", help="the 3D (D3Q125) entry alone")
+    ap.add_argument("--d3-cells", type=int, default=64, help="cells per axis of the 3D grid (p = 2)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -83,7 +83,7 @@ __device__ __forceinline__ void eq_point(const EqDerivs<T>& d, int a, int b, T* 
   *Eq = eq;
 }
 
-__global__ void __launch_bounds__(128) adjoint_collide_kernel(const __grid_constant__ AdjointArgs a) {
+__global__ void __launch_bounds__(128, 4) adjoint_collide_kernel(const __grid_constant__ AdjointArgs a) {
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= a.nv) return;
   const float rho = a.moments[v], ux = a.moments[a.nv + v], uy = a.moments[2 * a.nv + v],

@@ -468,8 +468,18 @@ def tgv3d(cells=64, order=2, ma=0.1, re=1600.0, steps=100):
                      dt, nu / dt + 0.5, steps, extra={"U0": ma})
 
 
+def _named(w, name):
+    w.name = name
+    return w
+
+
 ALL = {"tgv16": tgv16, "tgv256": tgv256, "sod": sod, "riemann": riemann,
-       "riemann_paper": riemann_paper, "riemann_glc": riemann_nodes,
+       "riemann_paper": riemann_paper,
+       # the same Table III problem on 512 x 512 cells (p = 3): a profiling case of the
+       # headline kernel with a state (2 x 472 MB) still larger than L2
+       "riemann_paper512": lambda: _named(riemann_paper().resized(512, 512, keep_tau=True),
+                                          "riemann512_p3_tableIII"),
+       "riemann_glc": riemann_nodes,
        "riemann_equidistant": lambda: riemann_nodes("equidistant"), "svi": svi, "svi_pr": svi_pr, "sdp": sdp,
        "tgv_moving": tgv_moving,
        # the moving vortex on 2048 x 2048 vertices (state larger than L2), both velocity sets

@@ -72,7 +72,8 @@ def test_host_validation_of_sizes_and_options():
         p = ok_params()
         setattr(p, field, value)
         assert create(ok_grid(), p) == status, (field, value)
-    # the 3D entry point: its own velocity set and FP64 only, checked before any CUDA call
+    # the 3D entry point: its own velocity set, FP64 or FP32 (no BF16 storage), checked before
+    # any CUDA call
     h3 = ctypes.c_void_p()
     g3 = sllbm.GridDesc3(2, 2, 2, 2, 0.0, 1.0, 0.0, 1.0, 0.0, 1.0, 0, 0, 0, 0)
     p3 = lambda **kw: sllbm.Params(kw.get("velset", sllbm.VEL_D3Q125), 0.01, 0.8, kw.get("cv", 2.5), 1.0,
@@ -80,7 +81,7 @@ def test_host_validation_of_sizes_and_options():
                                    kw.get("iso", 0))
     create3 = lambda g, p: lib.sllbm3d_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h3))
     assert create3(g3, p3(velset=0)) == sllbm.ERR_UNSUPPORTED
-    assert create3(g3, p3(prec=sllbm.PREC_F32)) == sllbm.ERR_UNSUPPORTED
+    assert create3(g3, p3(prec=sllbm.PREC_BF16_STORE)) == sllbm.ERR_UNSUPPORTED
     assert create3(g3, p3(pr=0.75)) == sllbm.ERR_UNSUPPORTED
     assert create3(g3, p3(iso=1)) == sllbm.ERR_ARG                 # isothermal needs cv = 3/2
     assert create3(g3, p3(cv=1.0)) == sllbm.ERR_ARG
