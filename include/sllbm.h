@@ -217,6 +217,15 @@ sllbm_status sllbm_moments_noalloc(const float* state_dev, int nx, int ny, doubl
                                    const double* A_dev, float* rho_dev, float* u_dev, float* v_dev,
                                    float* T_dev, double* mass_energy_dev, void* cuda_stream);
 
+/* Self-test of the bounded waits of the staging pipelines.  The paper has no counterpart: the
+ * TMA-staged step kernels wait on mbarriers for their staged tiles with an iteration limit, so
+ * that a copy that never lands makes sllbm_moments report SLLBM_ERR_CUDA ("a staging copy ...
+ * timed out") instead of hanging the GPU.  This call runs that wait, with a short limit, on an
+ * mbarrier nothing arrives on (no copy is involved) and returns SLLBM_OK if the wait ran out and
+ * reported it, SLLBM_ERR_CUDA otherwise.  Enqueues one small kernel on cuda_stream and
+ * synchronises it; allocates nothing (its flag is a device variable of the library). */
+sllbm_status sllbm_selftest_bounded_wait(void* cuda_stream);
+
 /* ------------------------------------------------------------------------------------------
  * 3D extension (the step the paper names as its next one): D3Q125, the tensor product of D1Q5
  * three times, on a uniform grid of hexahedral Lagrange cells of order 1..4 (Sec. II.E per axis),

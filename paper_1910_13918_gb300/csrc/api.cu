@@ -33,6 +33,8 @@ struct sllbm_ctx {
   ptrdiff_t ps = 0;
   void* dense = nullptr;                 // dense staging state for host transfers (on demand)
   cudaStream_t xfer = nullptr;           // copy stream of the host transfers (on demand)
+  cudaStream_t side = nullptr;           // fix-up launches beside the fused kernel (on demand)
+  cudaEvent_t side_ev[2] = {};
   cudaEvent_t xev[kXferChunks + 1] = {};
   AxisK ax{}, ay{};
   MapK map{};
@@ -581,6 +583,12 @@ const char* sllbm_last_error(const sllbm_ctx* c) { return c ? c->err.c_str() : "
 
 sllbm_status sllbm_destroy(sllbm_ctx* c) {
   if (!c) return SLLBM_ERR_ARG;
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+    for (int k = 0; k < 2; ++k)
+      if (c->side_ev[k]) cudaEventDestroy(c->side_ev[k]);
+  }
   if (c->xfer) {
     cudaStreamSynchronize(c->xfer);
     cudaStreamDestroy(c->xfer);
@@ -838,12 +846,29 @@ static cudaError_t enqueue_step(sllbm_ctx* c, float* mom = nullptr) {
   cudaError_t e;
   switch (c->kernel) {
     case kKernelUniform:
-      e = launch_step_uniform(a, c->ut, c->store, c->stream);
-      if (e == cudaSuccess && c->n_fix > 0) {  // vertices off the cell-periodic pattern
-        a.vlist = c->fix_list;
-        a.nlist = c->n_fix;
-        a.mapped = 0;
-        e = launch_step_gather(a, c->store, c->stream);
+      if (c->n_fix > 0) {
+        // vertices off the cell-periodic pattern: the gather kernel reads the same source and
+        // writes other vertices than the fused kernel, so it runs on a side stream beside it
+        // (filling the SMs the persistent kernel's tail leaves idle); the step ends when both do
+        if (!c->side) {
+          e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+          for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&c->side_ev[k], cudaEventDisableTiming);
+          if (e != cudaSuccess) return e;
+        }
+        if ((e = cudaEventRecord(c->side_ev[0], c->stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->side, c->side_ev[0], 0)) != cudaSuccess) return e;
+        e = launch_step_uniform(a, c->ut, c->store, c->stream);
+        if (e != cudaSuccess) return e;
+        StepArgs f = a;
+        f.vlist = c->fix_list;
+        f.nlist = c->n_fix;
+        f.mapped = 0;
+        if ((e = launch_step_gather(f, c->store, c->side)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(c->side_ev[1], c->side)) != cudaSuccess) return e;
+        e = cudaStreamWaitEvent(c->stream, c->side_ev[1], 0);
+      } else {
+        e = launch_step_uniform(a, c->ut, c->store, c->stream);
       }
       break;
     case kKernelMapped:

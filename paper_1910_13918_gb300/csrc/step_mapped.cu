@@ -112,8 +112,15 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
 #pragma unroll
     for (int ph = 0; ph < kQ1; ++ph) {
       const long s = s0 + ph;
-      mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);   // stage landed
-      __syncthreads();   // every thread is done with stage s - 1: its buffer can be refilled
+      const bool late = !mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);   // landed
+      // every thread is done with stage s - 1 (its buffer can be refilled); if the wait ran
+      // out, every thread stops together after the copies in flight for the next stages
+      if (__syncthreads_or(late)) {
+        const long last = s0 + (long)kQ1 * ((ntiles - tile + (int)gridDim.x - 1) / (int)gridDim.x);
+        for (long t = s + 1; t < s + PD && t < last; ++t)
+          if (!mbar_wait(&BAR[t % NSB], (unsigned)((t / NSB) & 1), a.flag)) break;
+        return;
+      }
       if (ph + PD < kQ1)
         issue(tile, ph + PD, s + PD);
       else

@@ -528,8 +528,17 @@ __global__ void __launch_bounds__(kNT) step_q9_tma_kernel(const __grid_constant_
 #pragma unroll
     for (int i = 0; i < kN; ++i) {
       const int ca = i / kN1, cb = i % kN1;
-      if (i % 3 == 0) mbar_wait(&BAR[buf * kQ9Groups + i / 3], parity, a.flag);   // group landed
-      if (i > 0) __syncthreads();   // every thread is past the previous plane's x pass (T free)
+      // group landed (every thread then also past the previous plane's x pass: T free); if the
+      // wait ran out, every thread stops together after the copies still in flight
+      const bool late = (i % 3 == 0) && !mbar_wait(&BAR[buf * kQ9Groups + i / 3], parity, a.flag);
+      if (__syncthreads_or(late)) {
+        for (int g = i / 3 + 1; g < kQ9Groups; ++g)   // this tile's later groups
+          if (!mbar_wait(&BAR[buf * kQ9Groups + g], parity, a.flag)) return;
+        if (k + 1 < my_tiles)                          // the next tile's groups
+          for (int g = 0; g < kQ9Groups; ++g)
+            if (!mbar_wait(&BAR[(buf ^ 1) * kQ9Groups + g], (unsigned)(((k + 1) >> 1) & 1), a.flag)) return;
+        return;
+      }
       const float* Si = Sb + (i / 3) * group_elems + (i % 3) * plane_elems;
 #pragma unroll
       for (int m = 0; m < kCC; ++m) {

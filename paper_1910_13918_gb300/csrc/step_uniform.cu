@@ -282,8 +282,14 @@ __global__ void __launch_bounds__(TileShape<P>::NT, TileShape<P>::MINB)
     for (int j = 0; j < kQ1; ++j) {
       if (!ycur && j > 0) break;   // after the last tile: its x pass of stage 4 and collision
       const int s = kQ1 * k + j;
-      if (ycur) mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);  // stage landed
-      __syncthreads();  // T[(s-1)&1] written; T[s&1] and S[(s+PD)%NSB] no longer read
+      const bool late = ycur && !mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);
+      // stage landed (or its wait ran out: then every thread stops together, after the copies
+      // still in flight for the next stages -- issued up to s + PD - 1 -- have landed)
+      if (__syncthreads_or(late)) {   // also: T[(s-1)&1] written; T[s&1], S[(s+PD)%NSB] free
+        for (int t = s + 1; t < s + PD && t < kQ1 * my_tiles; ++t)
+          if (!mbar_wait(&BAR[t % NSB], (unsigned)((t / NSB) & 1), a.flag)) break;
+        return;
+      }
       if (ycur) {
         if (j + PD < kQ1)
           issue(tile, j + PD, s + PD);

@@ -37,11 +37,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 // Wait for a phase of an mbarrier with an iteration limit; on timeout set bit 2 of *flag and
-// return (the results of the CTA are then garbage, but nothing hangs).
-__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned parity, int* flag) {
-  for (long it = 0; it < (1L << 22); ++it)
-    if (mbar_try_wait(bar, parity)) return;
+// return false (the kernels then stop their CTA: see step_uniform.cu), so nothing hangs.
+template <long Limit = (1L << 22)>
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* flag) {
+  for (long it = 0; it < Limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
   atomicOr(flag, 4);
+  return false;
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z,
                                             uint64_t* bar) {

@@ -30,6 +30,7 @@ EXPORTS = [
     "sllbm_init_equilibrium", "sllbm_step", "sllbm_step_moments", "sllbm_step_host", "sllbm_moments", "sllbm_get_state",
     "sllbm_set_state", "sllbm_adjoint_step", "sllbm_init_equilibrium_vjp", "sllbm_step_kernel_name",
     "sllbm_launches_per_step", "sllbm_status_string", "sllbm_last_error", "sllbm_moments_noalloc",
+    "sllbm_selftest_bounded_wait",
     "sllbm3d_create", "sllbm3d_destroy", "sllbm3d_grid_info", "sllbm3d_vertex_coords",
     "sllbm3d_precompute_departures", "sllbm3d_init_equilibrium", "sllbm3d_step", "sllbm3d_moments",
     "sllbm3d_get_state", "sllbm3d_set_state", "sllbm3d_last_error",
@@ -100,6 +101,7 @@ def load(path: str | None = None):
         "sllbm_status_string": ([I], ctypes.c_char_p),
         "sllbm_moments_noalloc": ([V, I, I, D, V, V, V, V, V, V, P], I),
         "sllbm_last_error": ([P], ctypes.c_char_p),
+        "sllbm_selftest_bounded_wait": ([P], I),
         "sllbm3d_create": ([ctypes.POINTER(GridDesc3), ctypes.POINTER(Params), P, ctypes.POINTER(P)], I),
         "sllbm3d_destroy": ([P], I),
         "sllbm3d_grid_info": ([P] + [ctypes.POINTER(I)] * 4, I),
