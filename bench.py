@@ -42,12 +42,12 @@ SECONDARY = "tgv256"          # second grid of the line: the Taylor-Green vortex
 # DRAM traffic (read + write bytes per launch) of the step kernel from an ncu capture, keyed by
 # (kernel source digest, workload, precision); reported as null once the kernel source changes.
 NCU_TRAFFIC = {
-    # 512^2-cell capture: 526.3 MB read + 429.7 MB written for 2,362,369 vertices, scaled by the
+    # 512^2-cell capture: 516.6 MB read + 429.1 MB written for 2,362,369 vertices, scaled by the
     # vertex count to the 3073^2 grid (a multi-pass capture of that grid exceeds the size rule)
-    ("e04b2b9fb294aa87", "riemann1024_p3_tableIII", "f32"): 956.04e6 * 9443329 / 2362369,
-    ("e04b2b9fb294aa87", "riemann512_p3_tableIII", "f32"): 956.04e6,
-    # full-size capture: 221.6 MB read + 174.7 MB written
-    ("e04b2b9fb294aa87", "tgv256_p4", "f32"): 396.3e6,
+    ("19f47ef50d49815d", "riemann1024_p3_tableIII", "f32"): 945.69e6 * 9443329 / 2362369,
+    ("19f47ef50d49815d", "riemann512_p3_tableIII", "f32"): 945.69e6,
+    # full-size capture: 219.3 MB read + 174.6 MB written
+    ("19f47ef50d49815d", "tgv256_p4", "f32"): 393.84e6,
 }
 
 # Sources that decide what the fused kernels of NCU_TRAFFIC do and how they are launched on
