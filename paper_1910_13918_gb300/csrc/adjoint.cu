@@ -83,39 +83,93 @@ __device__ __forceinline__ void eq_point(const EqDerivs<T>& d, int a, int b, T* 
   *Eq = eq;
 }
 
-__global__ void __launch_bounds__(128, 4) adjoint_collide_kernel(const __grid_constant__ AdjointArgs a) {
-  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= a.nv) return;
+// J_C^T through the Hermite moments of lambda.  With f^eq_ab = rho w_a w_b E_ab and the
+// factorised E_ab = sum_{k+l<=4} A_k(u_x) he[k][a] A_l(u_y) he[l][b], every sum over the 25
+// velocities of w_a w_b lambda_ab times E_ab or one of its derivatives in u_x, u_y, q is a
+// combination of the 15 moments M[k][l] = sum_ab (w_a he[k][a]) (w_b he[l][b]) lambda_ab,
+// k + l <= 4, with coefficients from A and its derivatives.  So the four reductions take 2 x 15
+// moments (of the f and g adjoints) and a few dozen products, not 25 evaluations of E and three
+// derivatives.  Result z = (dp/dm)^T y of the moment covector, scaled by omega.
+constexpr int kTri = 15;   // pairs (k, l) with k + l <= 4
+__device__ __forceinline__ constexpr int tri(int k, int l) { return k * 5 - k * (k - 1) / 2 + l; }
+
+__device__ __forceinline__ void axis_A(float u, float q, float (&A)[5], float (&Au)[5], float (&Aq)[5]) {
+  A[0] = 1.f;
+  A[1] = u;
+  A[2] = u * u + q;
+  A[3] = u * u * u + 3.f * u * q;
+  A[4] = u * u * u * u + 6.f * u * u * q + 3.f * q * q;
+  Au[0] = 0.f;
+  Au[1] = 1.f;
+  Au[2] = 2.f * u;
+  Au[3] = 3.f * u * u + 3.f * q;
+  Au[4] = 4.f * u * u * u + 12.f * u * q;
+  Aq[0] = 0.f;
+  Aq[1] = 0.f;
+  Aq[2] = 1.f;
+  Aq[3] = 3.f * u;
+  Aq[4] = 6.f * u * u + 6.f * q;
+}
+
+// omega z of vertex v (z of Eq. J_C^T: lambda_out = (1 - omega) lambda + omega M^T z).
+__device__ __forceinline__ float4 adjoint_z(const AdjointArgs& a, long long v) {
   const float rho = a.moments[v], ux = a.moments[a.nv + v], uy = a.moments[2 * a.nv + v],
               theta = a.moments[3 * a.nv + v];
   const float q = theta - 1.f, K = a.cp.Kf, cv = a.cp.cvf, om = a.cp.omegaf;
   const bool has_g = a.cp.npop == 2;
-  EqDerivs<float> d;
-  eq_derivs<float>(a.cs.hef, ux, uy, q, d);
-  // the vertex's 50 adjoint values, read once and kept in registers for both passes below
-  float lfv[kQ], lgv[kQ];
+  float Mf[kTri], Mg[kTri];
 #pragma unroll
-  for (int i = 0; i < kQ; ++i) {
-    lfv[i] = __ldg(a.lam_in + (size_t)i * a.nv + v);
-    lgv[i] = has_g ? __ldg(a.lam_in + (size_t)(kQ + i) * a.nv + v) : 0.f;
-  }
-  float yr = 0.f, yux = 0.f, yuy = 0.f, yth = 0.f;
+  for (int t = 0; t < kTri; ++t) Mf[t] = Mg[t] = 0.f;
 #pragma unroll
-  for (int ia = 0; ia < kQ1; ++ia)
+  for (int ia = 0; ia < kQ1; ++ia) {
+    float lf[kQ1], lg[kQ1];
 #pragma unroll
     for (int ib = 0; ib < kQ1; ++ib) {
-      const int i = 5 * ia + ib;
-      const float lf = lfv[i];
-      const float lg = lgv[i];
-      float E, Eux, Euy, Eq;
-      eq_point<float>(d, ia, ib, &E, &Eux, &Euy, &Eq);
-      const float w = a.cs.wf[ia] * a.cs.wf[ib];
-      const float L = lf + K * theta * lg;  // d(f^eq, g^eq)/dp contracted with lambda, f^eq part
-      yr += L * w * E;
-      yux += L * w * rho * Eux;
-      yuy += L * w * rho * Euy;
-      yth += L * w * rho * Eq + K * lg * w * rho * E;
+      lf[ib] = __ldg(a.lam_in + (size_t)(5 * ia + ib) * a.nv + v);
+      lg[ib] = has_g ? __ldg(a.lam_in + (size_t)(kQ + 5 * ia + ib) * a.nv + v) : 0.f;
     }
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      float rf = 0.f, rg = 0.f;
+#pragma unroll
+      for (int ib = 0; ib < kQ1; ++ib) {
+        rf = fmaf(a.cs.whf[l][ib], lf[ib], rf);
+        rg = fmaf(a.cs.whf[l][ib], lg[ib], rg);
+      }
+#pragma unroll
+      for (int k = 0; k + l <= 4; ++k) {
+        Mf[tri(k, l)] = fmaf(a.cs.whf[k][ia], rf, Mf[tri(k, l)]);
+        Mg[tri(k, l)] = fmaf(a.cs.whf[k][ia], rg, Mg[tri(k, l)]);
+      }
+    }
+  }
+  float Ax[5], Aux[5], Aqx[5], Ay[5], Auy[5], Aqy[5];
+  axis_A(ux, q, Ax, Aux, Aqx);
+  axis_A(uy, q, Ay, Auy, Aqy);
+  // y = sum_ab w_a w_b L_ab (E, rho dE/du_x, rho dE/du_y, rho dE/dq) + K rho sum w_a w_b lambda^g E,
+  // with L = lambda^f + K theta lambda^g, contracted along l first
+  float yE = 0.f, yux = 0.f, yuy = 0.f, yq = 0.f, yg = 0.f;
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    float sy = 0.f, suy = 0.f, sqy = 0.f, sg = 0.f;
+#pragma unroll
+    for (int l = 0; k + l <= 4; ++l) {
+      const float mL = fmaf(K * theta, Mg[tri(k, l)], Mf[tri(k, l)]);
+      sy = fmaf(Ay[l], mL, sy);
+      suy = fmaf(Auy[l], mL, suy);
+      sqy = fmaf(Aqy[l], mL, sqy);
+      sg = fmaf(Ay[l], Mg[tri(k, l)], sg);
+    }
+    yE = fmaf(Ax[k], sy, yE);
+    yux = fmaf(Aux[k], sy, yux);
+    yuy = fmaf(Ax[k], suy, yuy);
+    yq = fmaf(Aqx[k], sy, fmaf(Ax[k], sqy, yq));
+    yg = fmaf(Ax[k], sg, yg);
+  }
+  const float yr = yE;
+  yux *= rho;
+  yuy *= rho;
+  const float yth = rho * (yq + K * yg);
   // z = (dp/dm)^T y with m = (rho, j_x, j_y, e2), e2 = sum f|xi|^2 + sum g
   const float inv = 1.f / rho;
   const float u2 = ux * ux + uy * uy;
@@ -123,14 +177,35 @@ __global__ void __launch_bounds__(128, 4) adjoint_collide_kernel(const __grid_co
   const float z1 = yux * inv - yth * ux / cv * inv;
   const float z2 = yuy * inv - yth * uy / cv * inv;
   const float z3 = yth / (2.f * cv) * inv;
+  return make_float4(om * z0, om * z1, om * z2, om * z3);
+}
+
+// (f, g) of J_C^T lambda at velocity (cx, cy) from lambda and omega z.
+__device__ __forceinline__ float2 adjoint_mu(float lf, float lg, float4 z, float om1, float cx,
+                                             float cy, float c2, bool has_g) {
+  return make_float2(fmaf(om1, lf, fmaf(c2, z.w, fmaf(cy, z.z, fmaf(cx, z.y, z.x)))),
+                     has_g ? fmaf(om1, lg, z.w) : 0.f);
+}
+
+// J_C^T of every vertex: omega z into a.z (the one-pass S^T forms the (f, g) pairs itself), or,
+// with kWriteMu, the 25 (f, g) pairs into a.mu for the two-pass and mapped S^T.
+template <bool kWriteMu>
+__global__ void __launch_bounds__(128, 8) adjoint_collide_kernel(const __grid_constant__ AdjointArgs a) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= a.nv) return;
+  const float4 z = adjoint_z(a, v);
+  if (!kWriteMu) {
+    a.z[v] = z;
+    return;
+  }
+  const bool has_g = a.cp.npop == 2;
+  const float om1 = 1.f - a.cp.omegaf;
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const float cx = a.cs.xif[i / 5], cy = a.cs.xif[i % 5];
-    const float lf = lfv[i];
-    const float lg = lgv[i];
-    a.mu[(size_t)i * a.nv + v] =
-        make_float2((1.f - om) * lf + om * (z0 + z1 * cx + z2 * cy + z3 * (cx * cx + cy * cy)),
-                    has_g ? (1.f - om) * lg + om * z3 : 0.f);
+    const float lf = __ldg(a.lam_in + (size_t)i * a.nv + v);
+    const float lg = has_g ? __ldg(a.lam_in + (size_t)(kQ + i) * a.nv + v) : 0.f;
+    a.mu[(size_t)i * a.nv + v] = adjoint_mu(lf, lg, z, om1, cx, cy, cx * cx + cy * cy, has_g);
   }
 }
 
@@ -192,12 +267,14 @@ __global__ void __launch_bounds__(256) adjoint_stream_y_kernel(const __grid_cons
   }
 }
 
-// S^T on a uniform grid in one pass: a block takes a 32 x 32 tile of target vertices of one
-// velocity plane, loads the source region the transposed stencils reach (the tile and a halo of
-// H vertices on every side, wrapped on periodic axes) into shared memory, applies the x stencils
-// to every row of the region, then the y stencils to the tile.  Small blocks (one plane, few
-// registers) keep eight of them resident per SM, which hides the region loads.  The entries of each stencil are
-// the same as in the two-pass form and summed in the same order.
+// S^T on a uniform grid in one pass, with J_C^T folded into its loads: a block takes a 32 x 32
+// tile of target vertices of one velocity plane and forms the (f, g) pairs of J_C^T lambda on the
+// source region the transposed stencils reach (the tile and a halo of H vertices on every side,
+// wrapped on periodic axes) from lambda and omega z as it loads them into shared memory; then it
+// applies the x stencils to every row of the region and the y stencils to the tile.  Each warp
+// loads its region rows with all loads in flight at once (lane = column).  The velocity plane is
+// the fastest grid index, so the 25 blocks of one tile run close together and read z from L2.
+// The entries of each stencil are those of the two-pass form, summed in the same order.
 constexpr int kAT = 32;   // target tile edge of the fused S^T
 
 // Index of region row/column j on an axis of n vertices: wrapped on periodic axes (the region
@@ -214,21 +291,43 @@ __device__ __forceinline__ int wrap_or_clamp(int j, int n, int periodic) {
 }
 
 template <int KW, int H>
-__global__ void __launch_bounds__(256) adjoint_stream_fused_kernel(const __grid_constant__ AdjointArgs a) {
-  constexpr int RX = kAT + 2 * H, RY = kAT + 2 * H;
-  __shared__ float2 Sm[RY][RX];    // source region: rows y0-H.., columns x0-H..
+__global__ void __launch_bounds__(256, 3) adjoint_stream_fused_kernel(const __grid_constant__ AdjointArgs a) {
+  constexpr int RX = kAT + 2 * H, RY = kAT + 2 * H, NR = RY / 8;
+  static_assert(RY % 8 == 0 && 2 * H <= 32, "region rows per warp, second column segment");
+  __shared__ float2 Sm[RY][RX];    // J_C^T lambda on the source region: rows y0-H.., columns x0-H..
   __shared__ float2 Tm[RY][kAT];   // after the x stencils
   __shared__ int Yo[kAT][KW];      // y stencils of the tile's rows: source row - target row
   __shared__ float Yw[kAT][KW];
   __shared__ int Yd[kAT];
-  const int i = blockIdx.z, ia = i / 5, ib = i % 5;
-  const int x0 = blockIdx.x * kAT, y0 = blockIdx.y * kAT;
-  const float2* m = a.mu + (size_t)i * a.nv;
-  for (int e = threadIdx.x; e < RX * RY; e += 256) {
-    const int r = e / RX, cc = e - r * RX;
-    const int gy = wrap_or_clamp(y0 - H + r, a.ny, a.periodic_y);
-    const int gx = wrap_or_clamp(x0 - H + cc, a.nx, a.periodic_x);
-    Sm[r][cc] = __ldg(m + (size_t)gy * a.nx + gx);
+  const int i = blockIdx.x, ia = i / 5, ib = i % 5;
+  const int x0 = blockIdx.y * kAT, y0 = blockIdx.z * kAT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool has_g = a.cp.npop == 2;
+  const float* lfp = a.lam_in + (size_t)i * a.nv;
+  const float* lgp = a.lam_in + (size_t)(has_g ? kQ + i : i) * a.nv;
+  // this lane's region columns: H + lane - H.. and, for the first 2H lanes, the last 2H columns
+  const bool two = lane < 2 * H;
+  const int gxa = wrap_or_clamp(x0 - H + lane, a.nx, a.periodic_x);
+  const int gxb = wrap_or_clamp(x0 - H + kAT + (two ? lane : 0), a.nx, a.periodic_x);
+  float fa[NR], ga[NR], fb[NR], gb[NR];
+  float4 za[NR], zb[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const size_t row = (size_t)wrap_or_clamp(y0 - H + warp + 8 * j, a.ny, a.periodic_y) * a.nx;
+    fa[j] = __ldg(lfp + row + gxa);
+    ga[j] = __ldg(lgp + row + gxa);
+    za[j] = __ldg(a.z + row + gxa);
+    if (two) {
+      fb[j] = __ldg(lfp + row + gxb);
+      gb[j] = __ldg(lgp + row + gxb);
+      zb[j] = __ldg(a.z + row + gxb);
+    }
+  }
+  const float om1 = 1.f - a.cp.omegaf, cx = a.cs.xif[ia], cy = a.cs.xif[ib], c2 = cx * cx + cy * cy;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    Sm[warp + 8 * j][lane] = adjoint_mu(fa[j], ga[j], za[j], om1, cx, cy, c2, has_g);
+    if (two) Sm[warp + 8 * j][kAT + lane] = adjoint_mu(fb[j], gb[j], zb[j], om1, cx, cy, c2, has_g);
   }
   for (int e = threadIdx.x; e < kAT * KW; e += 256) {
     const int rr = e / KW, k = e - rr * KW, w = y0 + rr;
@@ -240,7 +339,7 @@ __global__ void __launch_bounds__(256) adjoint_stream_fused_kernel(const __grid_
     }
   }
   // the target column's transposed x stencil, as positions in a region row
-  const int c = threadIdx.x & 31, u = x0 + c;
+  const int u = x0 + lane;
   int xo[KW];
   float xw[KW];
   const int xdeg = u < a.nx ? __ldg(a.tx_deg + (size_t)ia * a.nx + u) : 0;
@@ -248,40 +347,44 @@ __global__ void __launch_bounds__(256) adjoint_stream_fused_kernel(const __grid_
   for (int k = 0; k < KW; ++k) {
     const bool on = k < xdeg;
     const size_t q = ((size_t)ia * a.nx + (on ? u : 0)) * KW + k;
-    xo[k] = H + c + (on ? __ldg(a.tx_rel + q) : 0);
+    xo[k] = H + lane + (on ? __ldg(a.tx_rel + q) : 0);
     xw[k] = on ? __ldg(a.tx_w + q) : 0.f;
   }
   __syncthreads();
-  for (int r = threadIdx.x >> 5; r < RY; r += 8) {
+  for (int r = warp; r < RY; r += 8) {
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < KW; ++k)
       if (k < xdeg) acc = fma2(bcast2(xw[k]), Sm[r][xo[k]], acc);
-    Tm[r][c] = acc;
+    Tm[r][lane] = acc;
   }
   __syncthreads();
   if (u >= a.nx) return;
-  for (int rr = threadIdx.x >> 5; rr < kAT; rr += 8) {
+  for (int rr = warp; rr < kAT; rr += 8) {
     const int w = y0 + rr;
     if (w >= a.ny) break;
     const int deg = Yd[rr];
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < KW; ++k)
-      if (k < deg) acc = fma2(bcast2(Yw[rr][k]), Tm[H + rr + Yo[rr][k]][c], acc);
+      if (k < deg) acc = fma2(bcast2(Yw[rr][k]), Tm[H + rr + Yo[rr][k]][lane], acc);
     const size_t t = (size_t)w * a.nx + u;
     a.lam_out[(size_t)i * a.nv + t] = acc.x;
-    a.lam_out[(size_t)(kQ + i) * a.nv + t] = (a.cp.npop == 2) ? acc.y : 0.f;
+    a.lam_out[(size_t)(kQ + i) * a.nv + t] = has_g ? acc.y : 0.f;
   }
 }
 
 template <int KW>
 static void launch_fused_kw(const AdjointArgs& a, cudaStream_t s) {
-  const dim3 grid((unsigned)((a.nx + kAT - 1) / kAT), (unsigned)((a.ny + kAT - 1) / kAT), kQ);
+  const dim3 grid(kQ, (unsigned)((a.nx + kAT - 1) / kAT), (unsigned)((a.ny + kAT - 1) / kAT));
   if (a.halo <= 4)
     adjoint_stream_fused_kernel<KW, 4><<<grid, 256, 0, s>>>(a);
   else
     adjoint_stream_fused_kernel<KW, 8><<<grid, 256, 0, s>>>(a);
+}
+
+bool adjoint_fused_usable(int nx, int ny, int halo) {
+  return halo <= 8 && (nx + kAT - 1) / kAT <= 65535 && (ny + kAT - 1) / kAT <= 65535;
 }
 
 // S^T on a mapped grid: CSR over the target vertex, per velocity.
@@ -300,14 +403,20 @@ __global__ void __launch_bounds__(256) adjoint_stream_mapped_kernel(const __grid
 }
 
 cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
-  adjoint_collide_kernel<<<(unsigned)((a.nv + 127) / 128), 128, 0, s>>>(a);
+  const unsigned cblocks = (unsigned)((a.nv + 127) / 128);
+  const bool fused = !a.mapped && a.z;   // the host gives z exactly when the one-pass S^T fits
+  if (fused)
+    adjoint_collide_kernel<false><<<cblocks, 128, 0, s>>>(a);
+  else
+    adjoint_collide_kernel<true><<<cblocks, 128, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)(a.ny < 65535 ? a.ny : 65535), kQ);
   if (a.mapped) {
     adjoint_stream_mapped_kernel<<<grid, 256, 0, s>>>(a);
-  } else if (a.halo <= 8 && (a.ny + kAT - 1) / kAT <= 65535) {
-    switch (a.kw) {   // one pass: x and y stencils through shared memory
+  } else if (fused) {
+    if (!adjoint_fused_usable(a.nx, a.ny, a.halo)) return cudaErrorInvalidValue;
+    switch (a.kw) {   // one pass: J_C^T pairs, x and y stencils through shared memory
       case 4: launch_fused_kw<4>(a, s); break;
       case 8: launch_fused_kw<8>(a, s); break;
       case 12: launch_fused_kw<12>(a, s); break;

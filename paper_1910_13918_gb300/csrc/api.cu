@@ -73,7 +73,8 @@ struct sllbm_ctx {
   int* flag = nullptr;
   // adjoint
   bool transposed = false;
-  float* mu = nullptr;
+  float* mu = nullptr;                                  // J_C^T pairs (two-pass and mapped S^T)
+  float* adjz = nullptr;                                // omega z per vertex (one-pass S^T)
   int *tx_col = nullptr, *ty_col = nullptr, tkw = 0;   // fixed-width transposed stencils
   int thalo = 0;                                        // their largest source-target offset
   int *tx_rel = nullptr, *ty_rel = nullptr;             // and each entry's offset
@@ -154,7 +155,10 @@ static void build_consts(Consts& cs, int velset) {
     }
     cs.xif[a] = (float)xi[a];
     cs.wf[a] = (float)w[a];
-    for (int k = 0; k < 5; ++k) cs.hef[k][a] = (float)cs.he[k][a];
+    for (int k = 0; k < 5; ++k) {
+      cs.hef[k][a] = (float)cs.he[k][a];
+      cs.whf[k][a] = (float)(cs.w[a] * cs.he[k][a]);
+    }
   }
   cs.inv_xi1f = (float)(1.0 / xi[1]);
   cs.xi1sqf = (float)(xi[1] * xi[1]);
@@ -1122,8 +1126,8 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
   if (!c->precomputed) return fail(c, SLLBM_ERR_STATE, "precompute_departures first");
   const bool mapped = c->map.kind != SLLBM_MAP_IDENTITY;
   if (!c->transposed) {
-    if (!c->mu) TRY(dalloc(c, &c->mu, (size_t)2 * kQ * c->nv));
     if (mapped) {
+      TRY(dalloc(c, &c->mu, (size_t)2 * kQ * c->nv));
       TRY(build_mapped_transpose(c));
     } else {
       AxisTranspose tx, ty;
@@ -1133,9 +1137,14 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
       if (kw > 16) return fail(c, SLLBM_ERR_UNSUPPORTED, "adjoint: more than 16 stencils read one node");
       TRY(upload_transpose(c, tx, c->nx, c->ax.periodic, kw, &c->tx_col, &c->tx_w, &c->tx_deg, &c->tx_rel));
       TRY(upload_transpose(c, ty, c->ny, c->ay.periodic, kw, &c->ty_col, &c->ty_w, &c->ty_deg, &c->ty_rel));
-      TRY(dalloc(c, &c->atmp, (size_t)kQ * c->nv));
       c->tkw = kw;
       c->thalo = std::max(tx.max_offset, ty.max_offset);
+      if (adjoint_fused_usable(c->nx, c->ny, c->thalo)) {
+        TRY(dalloc(c, &c->adjz, (size_t)4 * c->nv));   // omega z per vertex, 16 B
+      } else {
+        TRY(dalloc(c, &c->mu, (size_t)2 * kQ * c->nv));
+        TRY(dalloc(c, &c->atmp, (size_t)kQ * c->nv));
+      }
     }
     c->transposed = true;
   }
@@ -1143,6 +1152,7 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
   a.lam_in = lam_in;
   a.lam_out = lam_out;
   a.mu = reinterpret_cast<float2*>(c->mu);
+  a.z = reinterpret_cast<float4*>(c->adjz);
   a.moments = moments;
   a.nx = c->nx;
   a.ny = c->ny;

@@ -165,7 +165,8 @@ cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s);
 struct AdjointArgs {
   const float* lam_in;
   float* lam_out;
-  float2* mu;          // [25][nv] scratch: J_C^T lambda as (f, g) pairs
+  float2* mu;          // [25][nv] scratch: J_C^T lambda as (f, g) pairs (two-pass and mapped S^T)
+  float4* z;           // [nv] scratch: omega z of J_C^T per vertex (one-pass S^T); null otherwise
   const float* moments;  // [4][nv]
   int nx, ny;
   long long nv;
@@ -191,6 +192,8 @@ struct AdjointArgs {
   const float* tm_w;
 };
 cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s);
+// Whether the one-pass S^T takes a uniform grid with this transposed-stencil halo.
+bool adjoint_fused_usable(int nx, int ny, int halo);
 struct InitVjpArgs {
   const double *rho, *u, *v, *T;
   const float* lam;

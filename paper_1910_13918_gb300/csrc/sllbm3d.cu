@@ -442,7 +442,10 @@ void d1q5_consts(Consts& cs) {
     }
     cs.xif[a] = (float)xi[a];
     cs.wf[a] = (float)w[a];
-    for (int k = 0; k < kQ1; ++k) cs.hef[k][a] = (float)cs.he[k][a];
+    for (int k = 0; k < kQ1; ++k) {
+      cs.hef[k][a] = (float)cs.he[k][a];
+      cs.whf[k][a] = (float)(cs.w[a] * cs.he[k][a]);
+    }
   }
   cs.inv_xi1f = (float)(1.0 / xi[1]);
   cs.xi1sqf = (float)(xi[1] * xi[1]);

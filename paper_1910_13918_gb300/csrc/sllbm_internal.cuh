@@ -25,6 +25,7 @@ struct Consts {
   double xi[kQ1], w[kQ1];
   double he[kQ1][kQ1];
   float xif[kQ1], wf[kQ1], hef[kQ1][kQ1];
+  float whf[kQ1][kQ1];   // w_a he[k][a], FP32
   int nq1;   // 1D nodes of the set: 5 (D2Q25) or 3 (D2Q9); velocity i = nq1 a + b
   float inv_xi1f, xi1sqf;   // 1 / xi_1 and xi_1^2 (xi_1 the first nonzero node), FP32
 };
