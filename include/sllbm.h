@@ -182,8 +182,12 @@ sllbm_status sllbm_set_state(sllbm_ctx* ctx, const void* src_dev);
  * collision Jacobian at the pre-collision moments of that step, given as saved_moments
  * [4][ny][nx] FP32 = (rho, u, v, theta) -- exactly what sllbm_moments returns for the state the
  * step produced.  S^T is applied as a gather (pull) over precomputed transposed stencils: no
- * atomics, deterministic.  Works in every precision mode (FP32 arithmetic); a context with
- * Pr != 1 or the isothermal equilibrium gets SLLBM_ERR_UNSUPPORTED. */
+ * atomics, deterministic.  The first call builds the transposed stencils on the host and
+ * allocates the context's scratch for J_C^T lambda' (25 FP32 pairs a vertex, with ghost cells on
+ * uniform grids); later calls only enqueue.  A staging copy that does not land in time on uniform
+ * grids makes the next sllbm_moments return SLLBM_ERR_CUDA, as for the step.  Works in every
+ * precision mode (FP32 arithmetic); a context with Pr != 1 or the isothermal equilibrium gets
+ * SLLBM_ERR_UNSUPPORTED. */
 sllbm_status sllbm_adjoint_step(sllbm_ctx* ctx, const float* lambda_in_dev, float* lambda_out_dev,
                                 const float* saved_moments_dev);
 

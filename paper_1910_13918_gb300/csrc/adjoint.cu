@@ -8,7 +8,9 @@
 //   * S^T as a pull: every target vertex sums over the (vertex, weight) pairs of a precomputed
 //     transposed stencil (per axis on uniform grids, per velocity on transformed grids).  No
 //     atomics; the summation order is fixed, so results are deterministic.
-#include "kernels.h"
+#include <atomic>
+
+#include "tma.cuh"
 
 namespace sllbm {
 
@@ -187,25 +189,37 @@ __device__ __forceinline__ float2 adjoint_mu(float lf, float lg, float4 z, float
                      has_g ? fmaf(om1, lg, z.w) : 0.f);
 }
 
-// J_C^T of every vertex: omega z into a.z (the one-pass S^T forms the (f, g) pairs itself), or,
-// with kWriteMu, the 25 (f, g) pairs into a.mu for the two-pass and mapped S^T.
-template <bool kWriteMu>
-__global__ void __launch_bounds__(128, 8) adjoint_collide_kernel(const __grid_constant__ AdjointArgs a) {
+// J_C^T of every vertex: the 25 (f, g) pairs into mu, [25][mu_rows][mu_pitch] with mu_g ghost
+// columns and rows before the interior origin.  With ghost cells (the one-pass S^T), a vertex
+// within mu_g of a periodic edge also writes its periodic images there, so that the S^T regions
+// never wrap; the ghosts of non-periodic axes stay zero (never read).
+__global__ void __launch_bounds__(128, 7) adjoint_collide_kernel(const __grid_constant__ AdjointArgs a) {
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= a.nv) return;
   const float4 z = adjoint_z(a, v);
-  if (!kWriteMu) {
-    a.z[v] = z;
-    return;
-  }
   const bool has_g = a.cp.npop == 2;
   const float om1 = 1.f - a.cp.omegaf;
+  const int y = (int)(v / a.nx), x = (int)(v - (long long)y * a.nx), G = a.mu_g;
+  // the image column / row (the vertex's own when it has none); grids with ghosts have nx, ny >= 2G
+  int xi = x, yi = y;
+  if (G > 0 && a.periodic_x) xi = x < G ? x + a.nx : (x >= a.nx - G ? x - a.nx : x);
+  if (G > 0 && a.periodic_y) yi = y < G ? y + a.ny : (y >= a.ny - G ? y - a.ny : y);
+  const size_t plane = (size_t)a.mu_rows * a.mu_pitch;
+  float2* m = a.mu + (size_t)(G + y) * a.mu_pitch + (G + x);   // this vertex in plane 0
+  const int dx = xi - x, dy = (yi - y) * a.mu_pitch;           // to its images
 #pragma unroll
   for (int i = 0; i < kQ; ++i) {
     const float cx = a.cs.xif[i / 5], cy = a.cs.xif[i % 5];
     const float lf = __ldg(a.lam_in + (size_t)i * a.nv + v);
     const float lg = has_g ? __ldg(a.lam_in + (size_t)(kQ + i) * a.nv + v) : 0.f;
-    a.mu[(size_t)i * a.nv + v] = adjoint_mu(lf, lg, z, om1, cx, cy, cx * cx + cy * cy, has_g);
+    const float2 mu = adjoint_mu(lf, lg, z, om1, cx, cy, cx * cx + cy * cy, has_g);
+    float2* mi = m + (size_t)i * plane;
+    *mi = mu;
+    if (dx) mi[dx] = mu;
+    if (dy) {
+      mi[dy] = mu;
+      if (dx) mi[dy + dx] = mu;
+    }
   }
 }
 
@@ -267,124 +281,238 @@ __global__ void __launch_bounds__(256) adjoint_stream_y_kernel(const __grid_cons
   }
 }
 
-// S^T on a uniform grid in one pass, with J_C^T folded into its loads: a block takes a 32 x 32
-// tile of target vertices of one velocity plane and forms the (f, g) pairs of J_C^T lambda on the
-// source region the transposed stencils reach (the tile and a halo of H vertices on every side,
-// wrapped on periodic axes) from lambda and omega z as it loads them into shared memory; then it
-// applies the x stencils to every row of the region and the y stencils to the tile.  Each warp
-// loads its region rows with all loads in flight at once (lane = column).  The velocity plane is
-// the fastest grid index, so the 25 blocks of one tile run close together and read z from L2.
-// The entries of each stencil are those of the two-pass form, summed in the same order.
-constexpr int kAT = 32;   // target tile edge of the fused S^T
+// S^T on a uniform grid in one pass, persistent CTAs with Tensor Memory Accelerator staging.
+// A work item is a tile of 32 x TY target vertices of one velocity plane.  Its source region (the
+// tile and a halo of H vertices on every side) arrives as one tensor copy of the ghost-padded
+// pairs, and the dense y stencils of its rows as one bulk copy, both on the stage's mbarrier,
+// issued NS - 1 items ahead into a ring of NS stages so that the copies overlap the stencil work
+// of earlier items.  Items are ordered plane by plane, so the CTAs at work share the halos of
+// neighbouring tiles in L2.  The transposed stencils are taken dense by offset d in [-H, H] (zero
+// weights where a stencil has no entry), so that each thread slides a register window over the
+// region: in the x pass a half-warp takes a region row, a lane two neighbouring target columns
+// (2H + 2 pairs read as H + 1 16-byte loads); in the y pass a warp takes TY / 8 neighbouring
+// target rows, a lane one column.  TY makes both passes split evenly over the 8 warps.
+constexpr int kATX = 32;        // target tile width
+constexpr int kAdjNT = 256;     // threads of a CTA
+constexpr int kAdjStages = 2;   // stages of the copy ring
 
-// Index of region row/column j on an axis of n vertices: wrapped on periodic axes (the region
-// may reach several periods round on very small grids), clamped otherwise (clamped cells are
-// loaded but never read: transposed stencils of non-periodic axes stay inside the axis).
-__device__ __forceinline__ int wrap_or_clamp(int j, int n, int periodic) {
-  if (periodic) {
-    if (j < 0) j += n;
-    if (j >= n) j -= n;
-    if (j < 0 || j >= n) j = ((j % n) + n) % n;   // grids smaller than the region
-    return j;
+template <int H, int NS>
+struct AdjTmaShape {
+  static constexpr int TY = H == 4 ? 40 : 32;   // target rows: (TY + 2H) / 2 row pairs = 3 per warp
+  static constexpr int RX = kATX + 2 * H, RY = TY + 2 * H, RE = RX * RY;
+  static constexpr int D = 2 * H + 1, DW = (D + 3) / 4 * 4;   // offsets; dense row width
+  static constexpr int RPW = RY / 2 / (kAdjNT / 32), YPW = TY / (kAdjNT / 32);
+  // a stage: the region's pairs [RY][RX], then the dense y stencils of the tile's rows [TY][DW]
+  static constexpr size_t kStage = sizeof(float2) * RE + sizeof(float) * ((TY * DW + 31) / 32 * 32);
+  static constexpr size_t kBytes = 128 + NS * kStage + sizeof(float2) * RY * kATX + sizeof(uint64_t) * NS;
+  static_assert(RY % (2 * (kAdjNT / 32)) == 0 && TY % (kAdjNT / 32) == 0, "even split over the warps");
+  static_assert((sizeof(float2) * RE) % 128 == 0 && kStage % 128 == 0, "128-byte aligned copies");
+};
+
+// (plane, tile column, tile row) of a CTA's items, stepped by the grid size without divisions.
+struct AdjCursor {
+  int i, tx, ty;
+  __device__ __forceinline__ void init(int item, int ntiles, int tiles_x) {
+    i = item / ntiles;
+    const int t = item - i * ntiles;
+    ty = t / tiles_x;
+    tx = t - ty * tiles_x;
   }
-  return j < 0 ? 0 : (j >= n ? n - 1 : j);
+  __device__ __forceinline__ void next(int sx, int sy, int tiles_x, int tiles_y) {
+    tx += sx;
+    ty += sy;
+    if (tx >= tiles_x) {
+      tx -= tiles_x;
+      ++ty;
+    }
+    while (ty >= tiles_y) {
+      ty -= tiles_y;
+      ++i;
+    }
+  }
+};
+
+// The copies of one item into a stage, completing on bar.
+template <int H, int NS>
+__device__ __forceinline__ void adj_issue(const AdjointArgs& a, const CUtensorMap& mmap, unsigned char* stage,
+                                          uint64_t* bar, const AdjCursor& c) {
+  using SH = AdjTmaShape<H, NS>;
+  const int x0 = c.tx * kATX, y0 = c.ty * SH::TY, ib = c.i % 5;
+  const int rows = a.ny - y0 < SH::TY ? a.ny - y0 : SH::TY;
+  const unsigned wy_bytes = (unsigned)(rows * SH::DW * sizeof(float));   // a multiple of 16
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  mbar_expect_tx(bar, (unsigned)(SH::RE * sizeof(float2)) + wy_bytes);
+  // x in floats: 2 (mu_g + x0 - H), a multiple of 4 (16 bytes) as mu_g, x0 and H are even
+  tma_load_3d(stage, &mmap, 2 * (a.mu_g + x0 - H), a.mu_g + y0 - H, c.i, bar);
+  bulk_load(stage + SH::RE * sizeof(float2), a.ty_dense + ((size_t)ib * a.ny + y0) * SH::DW, wy_bytes, bar);
 }
 
-template <int KW, int H>
-__global__ void __launch_bounds__(256, 3) adjoint_stream_fused_kernel(const __grid_constant__ AdjointArgs a) {
-  constexpr int RX = kAT + 2 * H, RY = kAT + 2 * H, NR = RY / 8;
-  static_assert(RY % 8 == 0 && 2 * H <= 32, "region rows per warp, second column segment");
-  __shared__ float2 Sm[RY][RX];    // J_C^T lambda on the source region: rows y0-H.., columns x0-H..
-  __shared__ float2 Tm[RY][kAT];   // after the x stencils
-  __shared__ int Yo[kAT][KW];      // y stencils of the tile's rows: source row - target row
-  __shared__ float Yw[kAT][KW];
-  __shared__ int Yd[kAT];
-  const int i = blockIdx.x, ia = i / 5, ib = i % 5;
-  const int x0 = blockIdx.y * kAT, y0 = blockIdx.z * kAT;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+template <int H, int NS>
+__global__ void __launch_bounds__(kAdjNT, 4) adjoint_stream_tma_kernel(const __grid_constant__ AdjointArgs a,
+                                                                       const __grid_constant__ CUtensorMap mmap) {
+  using SH = AdjTmaShape<H, NS>;
+  constexpr int RX = SH::RX, RY = SH::RY, RE = SH::RE, D = SH::D, DW = SH::DW, TY = SH::TY;
+  extern __shared__ unsigned char adj_smem[];
+  unsigned char* base = adj_smem + ((128 - (smem_u32(adj_smem) & 127)) & 127);
+  float2* Tm = reinterpret_cast<float2*>(base + NS * SH::kStage);   // [RY][kATX], after the x stencils
+  uint64_t* BAR = reinterpret_cast<uint64_t*>(Tm + RY * kATX);      // [NS]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int half = lane >> 4, cp2 = 2 * (lane & 15);                // x pass: row of the pair, column pair
+  const int tiles_x = (a.nx + kATX - 1) / kATX, tiles_y = (a.ny + TY - 1) / TY, ntiles = tiles_x * tiles_y;
+  const int my = (kQ * ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int sx = (int)gridDim.x % tiles_x, sy = (int)gridDim.x / tiles_x;
   const bool has_g = a.cp.npop == 2;
-  const float* lfp = a.lam_in + (size_t)i * a.nv;
-  const float* lgp = a.lam_in + (size_t)(has_g ? kQ + i : i) * a.nv;
-  // this lane's region columns: H + lane - H.. and, for the first 2H lanes, the last 2H columns
-  const bool two = lane < 2 * H;
-  const int gxa = wrap_or_clamp(x0 - H + lane, a.nx, a.periodic_x);
-  const int gxb = wrap_or_clamp(x0 - H + kAT + (two ? lane : 0), a.nx, a.periodic_x);
-  float fa[NR], ga[NR], fb[NR], gb[NR];
-  float4 za[NR], zb[NR];
-#pragma unroll
-  for (int j = 0; j < NR; ++j) {
-    const size_t row = (size_t)wrap_or_clamp(y0 - H + warp + 8 * j, a.ny, a.periodic_y) * a.nx;
-    fa[j] = __ldg(lfp + row + gxa);
-    ga[j] = __ldg(lgp + row + gxa);
-    za[j] = __ldg(a.z + row + gxa);
-    if (two) {
-      fb[j] = __ldg(lfp + row + gxb);
-      gb[j] = __ldg(lgp + row + gxb);
-      zb[j] = __ldg(a.z + row + gxb);
-    }
-  }
-  const float om1 = 1.f - a.cp.omegaf, cx = a.cs.xif[ia], cy = a.cs.xif[ib], c2 = cx * cx + cy * cy;
-#pragma unroll
-  for (int j = 0; j < NR; ++j) {
-    Sm[warp + 8 * j][lane] = adjoint_mu(fa[j], ga[j], za[j], om1, cx, cy, c2, has_g);
-    if (two) Sm[warp + 8 * j][kAT + lane] = adjoint_mu(fb[j], gb[j], zb[j], om1, cx, cy, c2, has_g);
-  }
-  for (int e = threadIdx.x; e < kAT * KW; e += 256) {
-    const int rr = e / KW, k = e - rr * KW, w = y0 + rr;
-    if (w < a.ny) {
-      const size_t q = ((size_t)ib * a.ny + w) * KW + k;
-      Yo[rr][k] = __ldg(a.ty_rel + q);
-      Yw[rr][k] = __ldg(a.ty_w + q);
-      if (k == 0) Yd[rr] = __ldg(a.ty_deg + (size_t)ib * a.ny + w);
-    }
-  }
-  // the target column's transposed x stencil, as positions in a region row
-  const int u = x0 + lane;
-  int xo[KW];
-  float xw[KW];
-  const int xdeg = u < a.nx ? __ldg(a.tx_deg + (size_t)ia * a.nx + u) : 0;
-#pragma unroll
-  for (int k = 0; k < KW; ++k) {
-    const bool on = k < xdeg;
-    const size_t q = ((size_t)ia * a.nx + (on ? u : 0)) * KW + k;
-    xo[k] = H + lane + (on ? __ldg(a.tx_rel + q) : 0);
-    xw[k] = on ? __ldg(a.tx_w + q) : 0.f;
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) mbar_init(&BAR[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
-  for (int r = warp; r < RY; r += 8) {
-    float2 acc = make_float2(0.f, 0.f);
+  AdjCursor cur, nxt;   // the item in work; (thread 0) the next item to copy
+  cur.init((int)blockIdx.x, ntiles, tiles_x);
+  nxt = cur;
+  if (tid == 0)
+    for (int k = 0; k < NS - 1 && k < my; ++k) {
+      adj_issue<H, NS>(a, mmap, base + k * SH::kStage, &BAR[k], nxt);
+      nxt.next(sx, sy, tiles_x, tiles_y);
+    }
+#pragma unroll 1
+  for (int k = 0; k < my; ++k) {
+    if (k > 0) cur.next(sx, sy, tiles_x, tiles_y);
+    const int st = k % NS, i = cur.i, ia = i / 5;
+    const int x0 = cur.tx * kATX, y0 = cur.ty * TY;
+    // dense x stencils of this lane's two target columns (past the grid's last column, that
+    // column's: the outputs of those columns are not stored)
+    float wx0[D], wx1[D];
+    {
+      const int u0 = x0 + cp2;
+      const float* w0 = a.tx_dense + ((size_t)ia * a.nx + (u0 < a.nx ? u0 : a.nx - 1)) * DW;
+      const float* w1 = a.tx_dense + ((size_t)ia * a.nx + (u0 + 1 < a.nx ? u0 + 1 : a.nx - 1)) * DW;
 #pragma unroll
-    for (int k = 0; k < KW; ++k)
-      if (k < xdeg) acc = fma2(bcast2(xw[k]), Sm[r][xo[k]], acc);
-    Tm[r][lane] = acc;
-  }
-  __syncthreads();
-  if (u >= a.nx) return;
-  for (int rr = warp; rr < kAT; rr += 8) {
-    const int w = y0 + rr;
-    if (w >= a.ny) break;
-    const int deg = Yd[rr];
-    float2 acc = make_float2(0.f, 0.f);
+      for (int q = 0; q < DW; q += 4) {
+        const float4 v0 = __ldg(reinterpret_cast<const float4*>(w0 + q));
+        const float4 v1 = __ldg(reinterpret_cast<const float4*>(w1 + q));
+        const float e0[4] = {v0.x, v0.y, v0.z, v0.w}, e1[4] = {v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-    for (int k = 0; k < KW; ++k)
-      if (k < deg) acc = fma2(bcast2(Yw[rr][k]), Tm[H + rr + Yo[rr][k]][lane], acc);
-    const size_t t = (size_t)w * a.nx + u;
-    a.lam_out[(size_t)i * a.nv + t] = acc.x;
-    a.lam_out[(size_t)(kQ + i) * a.nv + t] = has_g ? acc.y : 0.f;
+        for (int m = 0; m < 4; ++m)
+          if (q + m < D) {
+            wx0[q + m] = e0[m];
+            wx1[q + m] = e1[m];
+          }
+      }
+    }
+    const bool late = !mbar_wait(&BAR[st], (unsigned)((k / NS) & 1), a.flag);
+    if (__syncthreads_or(late)) {
+      // a copy did not land in time: every thread stops, after waiting (bounded) for the copies
+      // still in flight into this CTA's stages
+      for (int t2 = k; t2 < k + NS - 1 && t2 < my; ++t2)
+        if (!mbar_wait(&BAR[t2 % NS], (unsigned)((t2 / NS) & 1), a.flag)) break;
+      return;
+    }
+    // every thread is past item k - 1: its stage takes item k + NS - 1
+    if (tid == 0 && k + NS - 1 < my) {
+      const int sn = (k + NS - 1) % NS;
+      adj_issue<H, NS>(a, mmap, base + sn * SH::kStage, &BAR[sn], nxt);
+      nxt.next(sx, sy, tiles_x, tiles_y);
+    }
+    const float2* Sm = reinterpret_cast<const float2*>(base + st * SH::kStage);
+    const float* Wy = reinterpret_cast<const float*>(Sm + RE);
+    // x pass: target columns cp2, cp2 + 1 of region row r read region columns cp2 .. cp2 + 2H + 1
+#pragma unroll
+    for (int j = 0; j < SH::RPW; ++j) {
+      const int r = 2 * (warp + j * (kAdjNT / 32)) + half;
+      const float4* src = reinterpret_cast<const float4*>(Sm + r * RX + cp2);
+      float2 win[2 * H + 2];
+#pragma unroll
+      for (int m = 0; m <= H; ++m) {
+        const float4 q = src[m];
+        win[2 * m] = make_float2(q.x, q.y);
+        win[2 * m + 1] = make_float2(q.z, q.w);
+      }
+      float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        a0 = fma2(bcast2(wx0[d]), win[d], a0);
+        a1 = fma2(bcast2(wx1[d]), win[d + 1], a1);
+      }
+      *reinterpret_cast<float4*>(Tm + r * kATX + cp2) = make_float4(a0.x, a0.y, a1.x, a1.y);
+    }
+    __syncthreads();
+    // y pass: target rows rr0 .. rr0 + YPW - 1 of column lane read Tm rows rr0 .. rr0 + YPW + 2H - 1
+    const int rr0 = SH::YPW * warp, u = x0 + lane;
+    float2 win[SH::YPW + 2 * H];
+#pragma unroll
+    for (int m = 0; m < SH::YPW + 2 * H; ++m) win[m] = Tm[(rr0 + m) * kATX + lane];
+#pragma unroll
+    for (int q = 0; q < SH::YPW; ++q) {
+      const int rr = rr0 + q, w = y0 + rr;
+      if (w < a.ny && u < a.nx) {
+        float wy[DW];
+#pragma unroll
+        for (int m = 0; m < DW; m += 4) {
+          const float4 v = reinterpret_cast<const float4*>(Wy + rr * DW)[m / 4];
+          wy[m] = v.x;
+          wy[m + 1] = v.y;
+          wy[m + 2] = v.z;
+          wy[m + 3] = v.w;
+        }
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int d = 0; d < D; ++d) acc = fma2(bcast2(wy[d]), win[q + d], acc);
+        const size_t o = (size_t)w * a.nx + u;
+        a.lam_out[(size_t)i * a.nv + o] = acc.x;
+        a.lam_out[(size_t)(kQ + i) * a.nv + o] = has_g ? acc.y : 0.f;
+      }
+    }
   }
 }
 
-template <int KW>
-static void launch_fused_kw(const AdjointArgs& a, cudaStream_t s) {
-  const dim3 grid(kQ, (unsigned)((a.nx + kAT - 1) / kAT), (unsigned)((a.ny + kAT - 1) / kAT));
-  if (a.halo <= 4)
-    adjoint_stream_fused_kernel<KW, 4><<<grid, 256, 0, s>>>(a);
-  else
-    adjoint_stream_fused_kernel<KW, 8><<<grid, 256, 0, s>>>(a);
+// Per device: SM count (cached) for the persistent grids.
+static int adj_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  int n = (dev >= 0 && dev < 64) ? cache[dev].load(std::memory_order_relaxed) : 0;
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 0;
+  if (dev >= 0 && dev < 64) cache[dev].store(n, std::memory_order_relaxed);
+  return n;
 }
 
-bool adjoint_fused_usable(int nx, int ny, int halo) {
-  return halo <= 8 && (nx + kAT - 1) / kAT <= 65535 && (ny + kAT - 1) / kAT <= 65535;
+template <int H>
+static cudaError_t launch_tma(const AdjointArgs& a, cudaStream_t s) {
+  using SH = AdjTmaShape<H, kAdjStages>;
+  auto kern = adjoint_stream_tma_kernel<H, kAdjStages>;
+  if (a.dhalo != H || a.dw != SH::DW) return cudaErrorInvalidValue;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // 3D map of the pairs as floats: (2 x column, row, velocity plane), ghost cells included
+  CUtensorMap mmap;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * a.mu_pitch, (cuuint64_t)a.mu_rows, (cuuint64_t)kQ};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.mu_pitch * sizeof(float2),
+                                 (cuuint64_t)a.mu_rows * a.mu_pitch * sizeof(float2)};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * SH::RX), (cuuint32_t)SH::RY, 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  if (enc(&mmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a.mu, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  // the shared-memory opt-in is per device: set it on every launch (a cheap host call)
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::kBytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjNT, SH::kBytes)) != cudaSuccess) return e;
+  const int n_sm = adj_sm_count();
+  if (per_sm < 1 || n_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long items = (long long)kQ * ((a.nx + kATX - 1) / kATX) * ((a.ny + SH::TY - 1) / SH::TY);
+  const long long grid = items < (long long)n_sm * per_sm ? items : (long long)n_sm * per_sm;
+  kern<<<(unsigned)grid, kAdjNT, SH::kBytes, s>>>(a, mmap);
+  return cudaGetLastError();
+}
+
+bool adjoint_tma_usable(int nx, int ny, int periodic_x, int periodic_y, int halo) {
+  const long long items = (long long)kQ * ((nx + kATX - 1) / kATX) * ((ny + 31) / 32);
+  return halo <= kAdjGhost && items < (1LL << 31) && (!periodic_x || nx >= 2 * kAdjGhost) &&
+         (!periodic_y || ny >= 2 * kAdjGhost) && encode_fn() != nullptr;
 }
 
 // S^T on a mapped grid: CSR over the target vertex, per velocity.
@@ -403,26 +531,15 @@ __global__ void __launch_bounds__(256) adjoint_stream_mapped_kernel(const __grid
 }
 
 cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s) {
-  const unsigned cblocks = (unsigned)((a.nv + 127) / 128);
-  const bool fused = !a.mapped && a.z;   // the host gives z exactly when the one-pass S^T fits
-  if (fused)
-    adjoint_collide_kernel<false><<<cblocks, 128, 0, s>>>(a);
-  else
-    adjoint_collide_kernel<true><<<cblocks, 128, 0, s>>>(a);
+  adjoint_collide_kernel<<<(unsigned)((a.nv + 127) / 128), 128, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((a.nx + 255) / 256), (unsigned)(a.ny < 65535 ? a.ny : 65535), kQ);
   if (a.mapped) {
     adjoint_stream_mapped_kernel<<<grid, 256, 0, s>>>(a);
-  } else if (fused) {
-    if (!adjoint_fused_usable(a.nx, a.ny, a.halo)) return cudaErrorInvalidValue;
-    switch (a.kw) {   // one pass: J_C^T pairs, x and y stencils through shared memory
-      case 4: launch_fused_kw<4>(a, s); break;
-      case 8: launch_fused_kw<8>(a, s); break;
-      case 12: launch_fused_kw<12>(a, s); break;
-      case 16: launch_fused_kw<16>(a, s); break;
-      default: return cudaErrorInvalidValue;
-    }
+  } else if (a.mu_g > 0) {   // ghost-padded pairs: the one-pass S^T (chosen by the host set-up)
+    if (a.mu_g != kAdjGhost || a.halo > kAdjGhost) return cudaErrorInvalidValue;
+    return a.dhalo == 4 ? launch_tma<4>(a, s) : launch_tma<8>(a, s);
   } else {
     const dim3 gx(grid.x, (unsigned)((a.ny + 15) / 16 < 65535 ? (a.ny + 15) / 16 : 65535), kQ);
     switch (a.kw) {   // x: 16 rows per thread, the column's stencil loaded once

@@ -74,10 +74,11 @@ struct sllbm_ctx {
   // adjoint
   bool transposed = false;
   float* mu = nullptr;                                  // J_C^T pairs (two-pass and mapped S^T)
-  float* adjz = nullptr;                                // omega z per vertex (one-pass S^T)
+  int mu_g = 0, mu_pitch = 0, mu_rows = 0;              // ghost-padded layout of mu (one-pass S^T)
   int *tx_col = nullptr, *ty_col = nullptr, tkw = 0;   // fixed-width transposed stencils
   int thalo = 0;                                        // their largest source-target offset
-  int *tx_rel = nullptr, *ty_rel = nullptr;             // and each entry's offset
+  float *tx_dense = nullptr, *ty_dense = nullptr;       // dense by offset (one-pass S^T)
+  int thalo_k = 0, tdw = 0;                             // its halo and row width
   int *tx_deg = nullptr, *ty_deg = nullptr;
   float2* atmp = nullptr;                               // between the x and y passes of S^T
   float *tx_w = nullptr, *ty_w = nullptr;
@@ -1021,11 +1022,9 @@ static sllbm_status axis_transpose(sllbm_ctx* c, const AxisK& ax, const int* off
 }
 
 // Fixed-width copy of a transpose: kw entries per (comp, node), padded with weight 0 on the node.
-// Also the entries' source - target offsets (the short way round a periodic axis), for the
-// one-pass S^T that reads sources from a region around the target tile.
-static sllbm_status upload_transpose(sllbm_ctx* c, const AxisTranspose& t, int n, bool periodic, int kw,
-                                     int** col_dev, float** w_dev, int** deg_dev, int** rel_dev) {
-  std::vector<int> col(t.rows.size() * kw), deg(t.rows.size()), rel(t.rows.size() * kw, 0);
+static sllbm_status upload_transpose(sllbm_ctx* c, const AxisTranspose& t, int n, int kw, int** col_dev,
+                                     float** w_dev, int** deg_dev) {
+  std::vector<int> col(t.rows.size() * kw), deg(t.rows.size());
   std::vector<float> wt(t.rows.size() * kw, 0.f);
   for (size_t r = 0; r < t.rows.size(); ++r) {
     deg[r] = (int)t.rows[r].size();
@@ -1033,24 +1032,35 @@ static sllbm_status upload_transpose(sllbm_ctx* c, const AxisTranspose& t, int n
       const bool have = (size_t)k < t.rows[r].size();
       col[r * kw + k] = have ? t.rows[r][k].first : (int)(r % n);
       wt[r * kw + k] = have ? t.rows[r][k].second : 0.f;
-      if (have) {
-        int d = t.rows[r][k].first - (int)(r % n);
-        if (periodic) {
-          if (d > n / 2) d -= n;
-          if (d < -n / 2) d += n;
-        }
-        rel[r * kw + k] = d;
-      }
     }
   }
   TRY(dalloc(c, col_dev, col.size()));
   TRY(dalloc(c, w_dev, wt.size()));
   TRY(dalloc(c, deg_dev, deg.size()));
-  TRY(dalloc(c, rel_dev, rel.size()));
-  CUDA_TRY(c, cudaMemcpy(*rel_dev, rel.data(), rel.size() * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(*col_dev, col.data(), col.size() * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(*w_dev, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice));
   CUDA_TRY(c, cudaMemcpy(*deg_dev, deg.data(), deg.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return SLLBM_OK;
+}
+
+// Dense copy of a transpose for the one-pass S^T: per (comp, node j), dw weights indexed by the
+// source offset d + h, d = source - j in [-h, h] (the short way round a periodic axis), 0 where
+// no entry has that offset.
+static sllbm_status upload_dense_transpose(sllbm_ctx* c, const AxisTranspose& t, int n, bool periodic, int h,
+                                           int dw, float** dense_dev) {
+  std::vector<float> dense(t.rows.size() * dw, 0.f);
+  for (size_t r = 0; r < t.rows.size(); ++r)
+    for (const auto& e : t.rows[r]) {
+      int d = e.first - (int)(r % n);
+      if (periodic) {
+        if (d > n / 2) d -= n;
+        if (d < -n / 2) d += n;
+      }
+      if (d < -h || d > h) return fail(c, SLLBM_ERR_UNSUPPORTED, "adjoint: stencil offset beyond the halo");
+      dense[r * dw + (d + h)] += e.second;
+    }
+  TRY(dalloc(c, dense_dev, dense.size()));
+  CUDA_TRY(c, cudaMemcpy(*dense_dev, dense.data(), dense.size() * sizeof(float), cudaMemcpyHostToDevice));
   return SLLBM_OK;
 }
 
@@ -1135,12 +1145,22 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
       TRY(axis_transpose(c, c->ay, c->offy, c->wy64, &ty));
       const int kw = (int)((std::max(tx.max_deg, ty.max_deg) + 3) / 4 * 4);   // 16-byte rows
       if (kw > 16) return fail(c, SLLBM_ERR_UNSUPPORTED, "adjoint: more than 16 stencils read one node");
-      TRY(upload_transpose(c, tx, c->nx, c->ax.periodic, kw, &c->tx_col, &c->tx_w, &c->tx_deg, &c->tx_rel));
-      TRY(upload_transpose(c, ty, c->ny, c->ay.periodic, kw, &c->ty_col, &c->ty_w, &c->ty_deg, &c->ty_rel));
+      TRY(upload_transpose(c, tx, c->nx, kw, &c->tx_col, &c->tx_w, &c->tx_deg));
+      TRY(upload_transpose(c, ty, c->ny, kw, &c->ty_col, &c->ty_w, &c->ty_deg));
       c->tkw = kw;
       c->thalo = std::max(tx.max_offset, ty.max_offset);
-      if (adjoint_fused_usable(c->nx, c->ny, c->thalo)) {
-        TRY(dalloc(c, &c->adjz, (size_t)4 * c->nv));   // omega z per vertex, 16 B
+      if (adjoint_tma_usable(c->nx, c->ny, c->ax.periodic, c->ay.periodic, c->thalo)) {
+        // ghost-padded pairs for the one-pass S^T; rows of a multiple of 4 pairs (32 bytes)
+        c->mu_g = kAdjGhost;
+        c->mu_pitch = (c->nx + 2 * kAdjGhost + 3) / 4 * 4;
+        c->mu_rows = c->ny + 2 * kAdjGhost;
+        const size_t n = (size_t)2 * kQ * c->mu_rows * c->mu_pitch;
+        TRY(dalloc(c, &c->mu, n));
+        CUDA_TRY(c, cudaMemsetAsync(c->mu, 0, n * sizeof(float), c->stream));   // ghosts never written
+        c->thalo_k = adjoint_tma_halo(c->thalo);
+        c->tdw = adjoint_dense_width(c->thalo_k);
+        TRY(upload_dense_transpose(c, tx, c->nx, c->ax.periodic, c->thalo_k, c->tdw, &c->tx_dense));
+        TRY(upload_dense_transpose(c, ty, c->ny, c->ay.periodic, c->thalo_k, c->tdw, &c->ty_dense));
       } else {
         TRY(dalloc(c, &c->mu, (size_t)2 * kQ * c->nv));
         TRY(dalloc(c, &c->atmp, (size_t)kQ * c->nv));
@@ -1152,7 +1172,10 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
   a.lam_in = lam_in;
   a.lam_out = lam_out;
   a.mu = reinterpret_cast<float2*>(c->mu);
-  a.z = reinterpret_cast<float4*>(c->adjz);
+  a.mu_g = c->mu_g;
+  a.mu_pitch = c->mu_g > 0 ? c->mu_pitch : c->nx;
+  a.mu_rows = c->mu_g > 0 ? c->mu_rows : c->ny;
+  a.flag = c->flag;
   a.moments = moments;
   a.nx = c->nx;
   a.ny = c->ny;
@@ -1171,8 +1194,10 @@ sllbm_status sllbm_adjoint_step(sllbm_ctx* c, const float* lam_in, float* lam_ou
   a.periodic_x = c->ax.periodic;
   a.periodic_y = c->ay.periodic;
   a.halo = c->thalo;
-  a.tx_rel = c->tx_rel;
-  a.ty_rel = c->ty_rel;
+  a.tx_dense = c->tx_dense;
+  a.ty_dense = c->ty_dense;
+  a.dhalo = c->thalo_k;
+  a.dw = c->tdw;
   a.tm_ptr = c->tm_ptr;
   a.tm_col = c->tm_col;
   a.tm_w = c->tm_w;

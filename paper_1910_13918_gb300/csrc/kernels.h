@@ -165,8 +165,12 @@ cudaError_t launch_moments(const MomentArgs& a, cudaStream_t s);
 struct AdjointArgs {
   const float* lam_in;
   float* lam_out;
-  float2* mu;          // [25][nv] scratch: J_C^T lambda as (f, g) pairs (two-pass and mapped S^T)
-  float4* z;           // [nv] scratch: omega z of J_C^T per vertex (one-pass S^T); null otherwise
+  // scratch: J_C^T lambda as (f, g) pairs, [25][mu_rows][mu_pitch] with mu_g ghost columns and
+  // rows before the interior origin: dense (mu_g = 0, pitch nx, ny rows) for the two-pass and
+  // mapped S^T, ghost-padded (mu_g = kAdjGhost, periodic images kept by J_C^T) for the one-pass S^T
+  float2* mu;
+  int mu_pitch, mu_rows, mu_g;
+  int* flag;           // bit 2: a staging copy of the one-pass S^T timed out
   const float* moments;  // [4][nv]
   int nx, ny;
   long long nv;
@@ -185,15 +189,24 @@ struct AdjointArgs {
   float2* tmp;         // [25][nv] scratch between the x and y passes of the uniform S^T
   int periodic_x, periodic_y;
   int halo;            // largest |source - target| of the uniform transposed stencils (wrapped)
-  const int* tx_rel;   // [5][nx][kw]: source - target of each entry, the short way round
-  const int* ty_rel;   // [5][ny][kw]
+  // one-pass S^T: the transposed stencils dense by offset, [5][n][dw] weights of the sources
+  // target + d, d in [-dhalo, dhalo] (the short way round), at d + dhalo
+  const float* tx_dense;
+  const float* ty_dense;
+  int dhalo, dw;
   const long long* tm_ptr;  // [25][nv+1]
   const int* tm_col;
   const float* tm_w;
 };
 cudaError_t launch_adjoint_step(const AdjointArgs& a, cudaStream_t s);
-// Whether the one-pass S^T takes a uniform grid with this transposed-stencil halo.
-bool adjoint_fused_usable(int nx, int ny, int halo);
+// Ghost width of the pairs of the one-pass S^T (its largest transposed-stencil halo), and whether
+// that kernel takes a uniform grid (halo, periodic axes at least two ghost widths long).
+constexpr int kAdjGhost = 8;
+bool adjoint_tma_usable(int nx, int ny, int periodic_x, int periodic_y, int halo);
+// The halo the one-pass S^T is compiled for (4 or 8) given the stencils' halo, and the row width
+// of its dense tables.
+inline int adjoint_tma_halo(int halo) { return halo <= 4 ? 4 : 8; }
+inline int adjoint_dense_width(int h) { return (2 * h + 1 + 3) / 4 * 4; }
 struct InitVjpArgs {
   const double *rho, *u, *v, *T;
   const float* lam;
