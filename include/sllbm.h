@@ -267,11 +267,20 @@ sllbm_status sllbm3d_precompute_departures(sllbm3d_ctx* ctx);
 sllbm_status sllbm3d_init_equilibrium(sllbm3d_ctx* ctx, const double* rho_dev, const double* u_dev,
                                       const double* v_dev, const double* w_dev, const double* T_dev);
 /* Advance nsteps steps (pull interpolation of every velocity with the tensor-product Lagrange
- * basis, moments, BGK); enqueues only. */
+ * basis, moments, BGK); enqueues only.  FP32 contexts of order 1 or 2 with an even number of x
+ * vertices and at least 36 x 12 x 8 vertices take the sum-factorised step (three launches:
+ * TMA-staged tiles that interpolate and sum the moments, a sweep that relaxes, a refresh of the
+ * periodic images in the state's ghost cells); the others the one-launch gather step.  The
+ * sum-factorised step keeps 2 ghost cells on every axis in its state and allocates 6 floats a
+ * vertex of scratch at sllbm3d_precompute_departures. */
 sllbm_status sllbm3d_step(sllbm3d_ctx* ctx, int nsteps);
+/* Name of the kernel sllbm3d_step uses for this context ("stream3d" for the sum-factorised FP32
+ * step, "gather_f32", "plain_f64"); valid after sllbm3d_precompute_departures. */
+const char* sllbm3d_step_kernel_name(const sllbm3d_ctx* ctx);
 /* rho, u, v, w, T of the current state (FP64 device arrays of nz*ny*nx, each may be NULL);
  * synchronises; SLLBM_ERR_UNSTABLE if a step or this call saw a non-positive or non-finite
- * density or temperature. */
+ * density or temperature, SLLBM_ERR_CUDA if a staging copy of the sum-factorised step did not
+ * land within its bounded wait. */
 sllbm_status sllbm3d_moments(sllbm3d_ctx* ctx, double* rho_dev, double* u_dev, double* v_dev,
                              double* w_dev, double* T_dev);
 /* Copy the state to / from a caller-owned device buffer of n_pop*125*nz*ny*nx doubles. */

@@ -19,6 +19,7 @@
 
 #include "../../include/sllbm.h"
 #include "kernels.h"
+#include "tma.cuh"
 
 using namespace sllbm;
 
@@ -40,11 +41,25 @@ struct Step3Args {
   int* flag;                             // bit 0: unstable
 };
 
+// Layout of an FP32 pair state: plane i, vertex (x, y, z) at
+// i * plane + origin + (z * rows + y) * pitch + x, with g ghost cells before the interior on
+// every axis (g = 0: the dense [125][nz][ny][nx]; the sum-factorised step keeps g = 2 and the
+// periodic images in the ghost cells, so that its staged regions never wrap).
+struct Pad3 {
+  int g, pitch, rows;
+  size_t plane, origin;
+  __host__ __device__ size_t at(int i, int x, int y, int z) const {
+    return (size_t)i * plane + origin + ((size_t)z * rows + y) * pitch + x;
+  }
+};
+
 struct Field3Args {
   const double *rho, *u, *v, *w, *T;     // init inputs
   double *orho, *ou, *ov, *ow, *oT;      // moment outputs
   double* state;                         // FP64: full populations [npop][125][nv]
-  float2* state32;                       // FP32: (f - w, g - K w) pairs [125][nv] (else null)
+  float2* state32;                       // FP32: (f - w, g - K w) pairs in layout lay (else null)
+  Pad3 lay;
+  int nx, ny;
   long long nv;
   Consts cs;
   double K, cv;
@@ -337,22 +352,435 @@ __global__ void __launch_bounds__(128) step3d_f32_kernel(const __grid_constant__
   if (!((rho > 0.f) && (qk > -1.f) && isfinite(rho) && isfinite(qk))) atomicOr(a.flag, 1);
 }
 
-// FP32 pairs <-> dense FP64 full populations [npop][125][nv].
-__global__ void convert3d_kernel(float2* pairs, double* dense, long long nv, int npop, double K,
-                                 Consts cs, int to_dense) {
+// ---- sum-factorised FP32 step (orders 1 and 2; an even number of x vertices, so that the
+// pair rows are whole 16-byte units for the tensor copies) ----
+//
+// Three launches a step.  stream3d_kernel: a CTA takes a tile of 32 x 8 x 4 vertices (two CTAs
+// an SM) and walks the
+// 125 velocity planes; per plane one TMA tensor copy brings the source region (the tile and the
+// stencil halo: x0 - 2 .. x0 + 33, and p on both sides in y and z), one plane ahead in two
+// stages.  The state keeps 2 ghost cells on every axis, holding the periodic images on periodic
+// axes (zero, and never read by an interior vertex, on zero-gradient ones), so a region never
+// wraps.  The interpolation is sum-factorised: z pass over the region's (y, x) columns, y pass
+// over the tile's z and the region's x, x pass into the destination, each in a centred tail-sum
+// form
+//   sum_d W_d v_{c+d} = v_c + sum_{j=1..p} T+_j (v_{c+j} - v_{c+j-1}) - sum_{j=1..p} T-_j (v_{c-j+1} - v_{c-j}),
+//   T+_j = sum_{d >= j} W_d, T-_j = sum_{d <= -j} W_d  (d the offset from the vertex, W_d its weight),
+// equal to the Lagrange sum because the weights sum to one and exact for constant fields in FP32.
+// The tile's tail sums of all five components are loaded once.  The thread of a vertex in the x
+// pass sums its moments over the 125 planes.  collide3d_kernel then relaxes every vertex's 125
+// pairs in place and writes the periodic images of the vertices next to periodic faces.
+constexpr int kT3X = 32, kT3Y = 8, kT3Z = 4, kT3NT = 256;
+constexpr int kT3XO = 2;   // the region starts at x0 - 2: 16-byte aligned for both orders
+constexpr int kT3G = 2;    // ghost cells of the state on every axis (>= the halo of p <= 2)
+
+template <int P>
+struct T3Shape {
+  static constexpr int RX = kT3X + 2 * kT3XO, RY = kT3Y + 2 * P, RZ = kT3Z + 2 * P;
+  static constexpr int RE = RX * RY * RZ;   // region pairs
+  static constexpr int NW = 2 * P;          // tail sums per (component, node): T+_1..p, -T-_1..p
+  static constexpr int ZT = RY * RX;        // z-pass columns
+  static constexpr int YT = kT3Z * RX;      // y-pass columns
+  static constexpr int NWT = kQ1 * (kT3Z + kT3Y + kT3X) * NW;   // the tile's tail sums
+  static constexpr size_t kStage = sizeof(float2) * RE;
+  static constexpr size_t kBytes = 128 + 2 * kStage +
+                                   sizeof(float2) * (size_t)(kT3Z * RY * RX + kT3Z * kT3Y * RX) +
+                                   sizeof(float) * NWT + sizeof(uint64_t) * 2;
+  static_assert(kStage % 128 == 0, "stages stay 128-byte aligned");
+  static constexpr int XR = kT3Y * kT3Z / (kT3NT / 32);   // x-pass rows per warp
+  static_assert(YT <= kT3NT && XR * (kT3NT / 32) == kT3Y * kT3Z, "one y column a thread, whole x rows a warp");
+  static_assert(P <= kT3G && kT3XO <= kT3G, "the halo stays within the ghost cells");
+};
+
+struct Stream3Args {
+  const float2* src;     // pairs in layout lay (deviations)
+  float2* dst;
+  Pad3 lay;
+  float* sums;           // [6][nv]: sum f, sum f xi_x, sum f xi_y, sum f xi_z, sum f |xi|^2, sum g
+  int nx, ny, nz;
+  long long nv;
+  const float* tx;       // [5][nx][2p] tail sums per (component, node)
+  const float* ty;
+  const float* tz;
+  Consts cs;
+  int* flag;             // bit 2: a staging copy timed out
+};
+
+// centred tail-sum interpolation at window position c (see above); w = T+_1..p, -T-_1..p
+template <int P, int N>
+__device__ __forceinline__ float2 tail_interp(const float2 (&v)[N], const float2 (&d)[N - 1], int c, const float* w) {
+  float2 acc = v[c];
+#pragma unroll
+  for (int j = 1; j <= P; ++j) {
+    acc = fma2(bcast2(w[j - 1]), d[c + j - 1], acc);
+    acc = fma2(bcast2(w[P + j - 1]), d[c - j], acc);
+  }
+  return acc;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kT3NT, 2) stream3d_kernel(const __grid_constant__ Stream3Args a,
+                                                            const __grid_constant__ CUtensorMap smap) {
+  using SH = T3Shape<P>;
+  constexpr int RX = SH::RX, RY = SH::RY, RZ = SH::RZ, RE = SH::RE, NW = SH::NW;
+  extern __shared__ unsigned char s3_smem[];
+  unsigned char* base = s3_smem + ((128 - (smem_u32(s3_smem) & 127)) & 127);
+  float2* S = reinterpret_cast<float2*>(base);                         // [2][RZ][RY][RX]
+  float2* Zb = S + 2 * RE;                                             // [TZ][RY][RX]
+  float2* Yb = Zb + kT3Z * RY * RX;                                    // [TZ][TY][RX]
+  float* Wz = reinterpret_cast<float*>(Yb + kT3Z * kT3Y * RX);         // [5][TZ][NW]
+  float* Wy = Wz + kQ1 * kT3Z * NW;                                    // [5][TY][NW]
+  float* Wx = Wy + kQ1 * kT3Y * NW;                                    // [5][TX][NW]
+  uint64_t* BAR = reinterpret_cast<uint64_t*>(Wx + kQ1 * kT3X * NW);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tiles_x = (a.nx + kT3X - 1) / kT3X, tiles_y = (a.ny + kT3Y - 1) / kT3Y;
+  const int byz = (int)blockIdx.x / tiles_x;
+  const int x0 = ((int)blockIdx.x - byz * tiles_x) * kT3X, y0 = (byz % tiles_y) * kT3Y,
+            z0 = (byz / tiles_y) * kT3Z;
+  // the tile's tail sums of all components (nodes past the grid clamped: those outputs are not
+  // stored)
+  for (int e = tid; e < SH::NWT; e += kT3NT) {
+    const int q = e % NW, r = e / NW;
+    float t;
+    if (r < kQ1 * kT3Z) {
+      const int c = r / kT3Z, n = min(z0 + r - c * kT3Z, a.nz - 1);
+      t = __ldg(a.tz + ((size_t)c * a.nz + n) * NW + q);
+    } else if (r < kQ1 * (kT3Z + kT3Y)) {
+      const int r2 = r - kQ1 * kT3Z, c = r2 / kT3Y, n = min(y0 + r2 - c * kT3Y, a.ny - 1);
+      t = __ldg(a.ty + ((size_t)c * a.ny + n) * NW + q);
+    } else {
+      const int r2 = r - kQ1 * (kT3Z + kT3Y), c = r2 / kT3X, n = min(x0 + r2 - c * kT3X, a.nx - 1);
+      t = __ldg(a.tx + ((size_t)c * a.nx + n) * NW + q);
+    }
+    Wz[e] = t;   // Wz, Wy and Wx are consecutive
+  }
+  if (tid == 0) {
+    mbar_init(&BAR[0], 1);
+    mbar_init(&BAR[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  // region origin in the ghost-padded layout: x0 - 2 + g (x in floats: 2 (x0 - 2 + g), a multiple
+  // of 4, i.e. 16 bytes), y0 - p + g, z0 - p + g
+  const int cx = 2 * (x0 - kT3XO + a.lay.g), cy = y0 - P + a.lay.g, cz = z0 - P + a.lay.g;
+  auto issue = [&](int i, int st) {   // thread 0: plane i into stage st
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    mbar_expect_tx(&BAR[st], (unsigned)SH::kStage);
+    tma_load_4d(S + (size_t)st * RE, &smap, cx, cy, cz, i, &BAR[st]);
+  };
+  if (tid == 0) issue(0, 0);
+  // x pass: warp w takes the tile rows XR w .. XR w + XR - 1 (row r: z = r / TY, y = r % TY),
+  // lane = x
+  constexpr int XR = SH::XR;
+  const int vx = x0 + lane;
+  float m[XR][6];
+#pragma unroll
+  for (int j = 0; j < XR; ++j)
+#pragma unroll
+    for (int q = 0; q < 6; ++q) m[j][q] = 0.f;
+  float wx[NW];
+#pragma unroll 1
+  for (int i = 0; i < kQ3; ++i) {
+    const int st = i & 1, ia = i / 25, ib = (i / 5) % 5, ic = i % 5;
+    const bool late = !mbar_wait(&BAR[st], (unsigned)((i >> 1) & 1), a.flag);
+    if (__syncthreads_or(late)) {   // the copy of plane i did not land in time: stop, after it
+      mbar_wait(&BAR[st], (unsigned)((i >> 1) & 1), a.flag);
+      return;
+    }
+    if (tid == 0 && i + 1 < kQ3) issue(i + 1, st ^ 1);   // every thread is past plane i - 1
+    if (ic == 0 && ib == 0) {   // a new x component: this lane's x tail sums
+#pragma unroll
+      for (int q = 0; q < NW; ++q) wx[q] = Wx[(ia * kT3X + lane) * NW + q];
+    }
+    const float2* Sst = S + (size_t)st * RE;
+    // z pass: column (ry, rx) of the region, the tile's z rows
+    const float* wz = Wz + ic * kT3Z * NW;
+    for (int t = tid; t < SH::ZT; t += kT3NT) {
+      float2 v[RZ], d[RZ - 1];
+#pragma unroll
+      for (int r = 0; r < RZ; ++r) v[r] = Sst[r * RY * RX + t];
+#pragma unroll
+      for (int r = 0; r + 1 < RZ; ++r) d[r] = sub2(v[r + 1], v[r]);
+#pragma unroll
+      for (int tz = 0; tz < kT3Z; ++tz) Zb[tz * RY * RX + t] = tail_interp<P>(v, d, tz + P, wz + tz * NW);
+    }
+    __syncthreads();
+    // y pass: column (tz, rx), the tile's y rows
+    if (tid < SH::YT) {
+      const int tz = tid / RX, rx = tid - tz * RX;
+      const float* wy = Wy + ib * kT3Y * NW;
+      float2 v[RY], d[RY - 1];
+#pragma unroll
+      for (int r = 0; r < RY; ++r) v[r] = Zb[(tz * RY + r) * RX + rx];
+#pragma unroll
+      for (int r = 0; r + 1 < RY; ++r) d[r] = sub2(v[r + 1], v[r]);
+#pragma unroll
+      for (int ty = 0; ty < kT3Y; ++ty) Yb[(tz * kT3Y + ty) * RX + rx] = tail_interp<P>(v, d, ty + P, wy + ty * NW);
+    }
+    __syncthreads();
+    // x pass: the vertex (x0 + lane, row) into the destination; its moments
+    const float ex = a.cs.xif[ia], ey = a.cs.xif[ib], ez = a.cs.xif[ic];
+    const float e2 = ex * ex + ey * ey + ez * ez;
+#pragma unroll
+    for (int j = 0; j < XR; ++j) {
+      const int r = XR * warp + j, tz = r / kT3Y, ty = r - tz * kT3Y;
+      const float2* row = Yb + (tz * kT3Y + ty) * RX + kT3XO + lane;
+      float2 v[2 * P + 1], d[2 * P];
+#pragma unroll
+      for (int k = 0; k <= 2 * P; ++k) v[k] = row[k - P];
+#pragma unroll
+      for (int k = 0; k < 2 * P; ++k) d[k] = sub2(v[k + 1], v[k]);
+      const float2 acc = tail_interp<P>(v, d, P, wx);
+      const int vy = y0 + ty, vz = z0 + tz;
+      if (vx < a.nx && vy < a.ny && vz < a.nz) {
+        a.dst[a.lay.at(i, vx, vy, vz)] = acc;
+        m[j][0] += acc.x;
+        m[j][1] += ex * acc.x;
+        m[j][2] += ey * acc.x;
+        m[j][3] += ez * acc.x;
+        m[j][4] += e2 * acc.x;
+        m[j][5] += acc.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < XR; ++j) {
+    const int r = XR * warp + j, tz = r / kT3Y, ty = r - tz * kT3Y;
+    const int vy = y0 + ty, vz = z0 + tz;
+    if (vx < a.nx && vy < a.ny && vz < a.nz) {
+      const size_t v = ((size_t)vz * a.ny + vy) * a.nx + vx;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) a.sums[(size_t)q * a.nv + v] = m[j][q];
+    }
+  }
+}
+
+// Second sweep of the sum-factorised step: one thread per vertex relaxes its 125 pairs in place
+// (read back from the destination, a row of 5 ahead), from the moment sums of the stream
+// kernel, with the residual correction of step3d_f32_kernel.  ghost_refresh3d_kernel then copies
+// the periodic images into the ghost cells.
+struct Collide3Args {
+  float2* dst;
+  Pad3 lay;
+  const float* sums;
+  int nx, ny, nz, px, py, pz;
+  long long nv;
+  Consts cs;
+  float omega, K, cv, inv2cv;
+  int npop, iso;
+  int* flag;
+};
+
+__global__ void __launch_bounds__(128, 6) collide3d_kernel(const __grid_constant__ Collide3Args a) {
+  const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= a.nv) return;
+  const int x = (int)(v % a.nx), y = (int)((v / a.nx) % a.ny), z = (int)(v / ((long long)a.nx * a.ny));
+  const size_t plane = a.lay.plane;
+  float2* own = a.dst + a.lay.at(0, x, y, z);
+  const size_t sp = (size_t)a.nv;
+  const float drho = a.sums[v], jx = a.sums[sp + v], jy = a.sums[2 * sp + v], jz = a.sums[3 * sp + v],
+              a2 = a.sums[4 * sp + v];
+  const float G = a.npop == 2 ? a.sums[5 * sp + v] : 0.f;
+  const float rho = 1.f + drho, inv_rho = __frcp_rn(rho);
+  const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+  const float qk = (a2 + G - rho * (ux * ux + uy * uy + uz * uz) - 2.f * a.cv * drho) * inv_rho * a.inv2cv;
+  const float q = a.iso ? 0.f : qk;
+  float Ax[5], Ay[5], Az[5];
+  {
+    const float u3[3] = {ux, uy, uz};
+    float* A3[3] = {Ax, Ay, Az};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float u = u3[d];
+      A3[d][0] = 1.f;
+      A3[d][1] = u;
+      A3[d][2] = u * u + q;
+      A3[d][3] = u * (u * u + 3.f * q);
+      A3[d][4] = u * u * (u * u + 6.f * q) + 3.f * q * q;
+    }
+  }
+  float Zc[5][5];   // [n][c]: sum_{m <= n} A_m(u_z) he_m(c)
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      acc += Az[m] * a.cs.hef[m][c];
+      Zc[m][c] = acc;
+    }
+  }
+  const float om = a.omega, Kq1 = a.K * (1.f + q), Kq = a.K * q;
+  const float2 om2 = bcast2(om);
+  float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3 = 0.f, re = 0.f;
+  // rows (a, b) of 5 pairs (c = 0..4), the next row's loads in flight while one row relaxes
+  float2 cur[kQ1];
+#pragma unroll
+  for (int ic = 0; ic < kQ1; ++ic) cur[ic] = own[(size_t)ic * plane];
+#pragma unroll 1
+  for (int row = 0; row < kQ1 * kQ1; ++row) {
+    const int ia = row / kQ1, ib = row - kQ1 * ia;
+    float2 nxt[kQ1];
+    if (row + 1 < kQ1 * kQ1) {
+#pragma unroll
+      for (int ic = 0; ic < kQ1; ++ic) nxt[ic] = own[(size_t)(kQ1 * (row + 1) + ic) * plane];
+    }
+    float Xa[5], Yb[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      Xa[k] = Ax[k] * a.cs.hef[k][ia];
+      Yb[k] = Ay[k] * a.cs.hef[k][ib];
+    }
+    const float ex = a.cs.xif[ia], ey = a.cs.xif[ib], wab = a.cs.wf[ia] * a.cs.wf[ib];
+    float2* o5 = own + (size_t)(kQ1 * row) * plane;
+#pragma unroll
+    for (int ic = 0; ic < kQ1; ++ic) {
+      float s1 = 0.f;
+#pragma unroll
+      for (int k = 0; k <= 4; ++k) {
+        float sl = 0.f;
+#pragma unroll
+        for (int l = 0; l <= 4 - k; ++l) sl += Yb[l] * Zc[4 - k - l][ic];
+        s1 += Xa[k] * sl;
+      }
+      const float w = wab * a.cs.wf[ic];
+      const float ef = w * (drho + rho * (s1 - 1.f));
+      const float eg = Kq1 * ef + Kq * w;
+      const float2 d = sub2(make_float2(ef, a.npop == 2 ? eg : 0.f), cur[ic]);
+      const float ez = a.cs.xif[ic];
+      r0 += d.x;
+      r1 += ex * d.x;
+      r2 += ey * d.x;
+      r3 += ez * d.x;
+      re += (ex * ex + ey * ey + ez * ez) * d.x + d.y;
+      o5[(size_t)ic * plane] = fma2(om2, d, cur[ic]);
+    }
+    if (row + 1 < kQ1 * kQ1) {
+#pragma unroll
+      for (int ic = 0; ic < kQ1; ++ic) cur[ic] = nxt[ic];
+    }
+  }
+  {
+    const float inv_s = a.cs.inv_xi1f, s2 = a.cs.xi1sqf;
+    const float d1 = r1 * inv_s, d2 = r2 * inv_s, d3 = r3 * inv_s;
+    const float d0 = r0 - d1 - d2 - d3;
+    const float de = re - s2 * (d1 + d2 + d3);
+    own[0].x -= om * d0;
+    own[25 * plane].x -= om * d1;
+    own[5 * plane].x -= om * d2;
+    own[1 * plane].x -= om * d3;
+    if (a.npop == 2) {
+      own[0].y -= om * de;
+    } else if (!a.iso) {
+      const float e = om * 0.5f * de * inv_s * inv_s;
+      own[25 * plane].x -= e;
+      own[75 * plane].x -= e;
+      own[0].x += 2.f * e;
+    }
+  }
+  if (!((rho > 0.f) && (qk > -1.f) && isfinite(rho) && isfinite(qk))) atomicOr(a.flag, 1);
+}
+
+// The periodic images of the ghost cells of a padded pair state, one thread per (plane, ghost
+// cell).  The ghost cells of a plane are enumerated as three disjoint sets: the 2g slices before
+// and after the interior slices (whole rows), then in the interior slices the 2g ghost rows,
+// then in the interior rows the 2g ghost columns.  A cell past a zero-gradient face is skipped.
+__global__ void __launch_bounds__(256) ghost_refresh3d_kernel(float2* pairs, Pad3 lay, int nx, int ny, int nz,
+                                                              int px, int py, int pz, long long per_plane) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)kQ3 * per_plane) return;
+  const int i = (int)(e / per_plane);
+  long long r = e - (long long)i * per_plane;
+  const int g = lay.g, W = lay.pitch, R = lay.rows;
+  const long long nzs = 2LL * g * R * W, nys = (long long)nz * 2 * g * W;
+  int X, Y, Z;   // interior coordinates of the ghost cell (outside [0, n) on some axis)
+  if (r < nzs) {
+    const int zz = (int)(r / ((long long)R * W));
+    r -= (long long)zz * R * W;
+    Z = zz < g ? zz - g : nz + zz - g;
+    Y = (int)(r / W) - g;
+    X = (int)(r % W) - g;
+  } else if ((r -= nzs) < nys) {
+    Z = (int)(r / (2LL * g * W));
+    r -= (long long)Z * 2 * g * W;
+    const int yy = (int)(r / W);
+    Y = yy < g ? yy - g : ny + yy - g;
+    X = (int)(r % W) - g;
+  } else {
+    r -= nys;
+    Z = (int)(r / ((long long)ny * 2 * g));
+    r -= (long long)Z * ny * 2 * g;
+    Y = (int)(r / (2 * g));
+    const int xx = (int)(r % (2 * g));
+    X = xx < g ? xx - g : nx + xx - g;
+  }
+  const bool ox = X < 0 || X >= nx, oy = Y < 0 || Y >= ny, oz = Z < 0 || Z >= nz;
+  if ((ox && !px) || (oy && !py) || (oz && !pz)) return;
+  const int x = ox ? (X < 0 ? X + nx : X - nx) : X, y = oy ? (Y < 0 ? Y + ny : Y - ny) : Y,
+            z = oz ? (Z < 0 ? Z + nz : Z - nz) : Z;
+  pairs[lay.at(i, X, Y, Z)] = pairs[lay.at(i, x, y, z)];
+}
+
+// Tail sums T+_j, -T-_j (j = 1..p) of every (component, node) of one axis, from the FP64 tables:
+// the stencil of node n starts at n + off and has weights w_0..w_p, offsets d = off + k.
+template <int P>
+__global__ void tail_table_kernel(const int* off, const double* w, int n, float* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kQ1 * n) return;
+  double W[2 * P + 1];
+#pragma unroll
+  for (int d = 0; d <= 2 * P; ++d) W[d] = 0.0;
+  const int o = off[e];
+#pragma unroll
+  for (int k = 0; k <= P; ++k) W[o + k + P] += w[(size_t)e * (P + 1) + k];   // o + k in [-P, P]
+#pragma unroll
+  for (int j = 1; j <= P; ++j) {
+    double tp = 0.0, tm = 0.0;
+    for (int d = j; d <= P; ++d) tp += W[d + P];
+    for (int d = -P; d <= -j; ++d) tm += W[d + P];
+    out[(size_t)e * 2 * P + j - 1] = (float)tp;
+    out[(size_t)e * 2 * P + P + j - 1] = (float)(-tm);
+  }
+}
+
+// FP32 pairs (layout lay) <-> dense FP64 full populations [npop][125][nv].
+__global__ void convert3d_kernel(float2* pairs, Pad3 lay, double* dense, int nx, int ny, long long nv, int npop,
+                                 double K, Consts cs, int to_dense) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)kQ3 * nv) return;
   const int i = (int)(e / nv);
+  const long long v = e - (long long)i * nv;
+  const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / ((long long)nx * ny));
+  const size_t o = lay.at(i, x, y, z);
   const double w = cs.w[i / 25] * cs.w[(i / 5) % 5] * cs.w[i % 5];
   if (to_dense) {
-    const float2 p = pairs[e];
+    const float2 p = pairs[o];
     dense[e] = (double)p.x + w;
     if (npop == 2) dense[(size_t)kQ3 * nv + e] = (double)p.y + K * w;
   } else {
     const float f = (float)(dense[e] - w);
     const float g = npop == 2 ? (float)(dense[(size_t)kQ3 * nv + e] - K * w) : 0.f;
-    pairs[e] = make_float2(f, g);
+    pairs[o] = make_float2(f, g);
   }
+}
+
+// Periodic images of a ghost-padded pair state: every ghost cell whose position lies past
+// periodic faces only takes the value of the interior vertex it images (ghosts past a
+// zero-gradient face stay as they are: zero, never read by an interior vertex).
+__global__ void ghost3d_kernel(float2* pairs, Pad3 lay, int nx, int ny, int nz, int px, int py, int pz) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int slices = nz + 2 * lay.g;
+  const long long per_plane = (long long)lay.pitch * lay.rows * slices;
+  if (e >= (long long)kQ3 * per_plane) return;
+  const int i = (int)(e / per_plane);
+  const long long r = e - (long long)i * per_plane;
+  const int X = (int)(r % lay.pitch) - lay.g, Y = (int)((r / lay.pitch) % lay.rows) - lay.g,
+            Z = (int)(r / ((long long)lay.pitch * lay.rows)) - lay.g;
+  const bool ox = X < 0 || X >= nx, oy = Y < 0 || Y >= ny, oz = Z < 0 || Z >= nz;
+  if (!(ox || oy || oz) || X >= nx + lay.g) return;   // interior, or row padding past the ghosts
+  if ((ox && !px) || (oy && !py) || (oz && !pz)) return;
+  const int x = ox ? (X < 0 ? X + nx : X - nx) : X, y = oy ? (Y < 0 ? Y + ny : Y - ny) : Y,
+            z = oz ? (Z < 0 ? Z + nz : Z - nz) : Z;
+  pairs[(size_t)i * lay.plane + r] = pairs[lay.at(i, x, y, z)];
 }
 
 __global__ void init3d_kernel(const __grid_constant__ Field3Args a) {
@@ -364,11 +792,12 @@ __global__ void init3d_kernel(const __grid_constant__ Field3Args a) {
   hermite_moments(a.v[v], q, Ay);
   hermite_moments(a.w[v], q, Az);
   const size_t plane = (size_t)a.nv;
+  const int x = (int)(v % a.nx), y = (int)((v / a.nx) % a.ny), z = (int)(v / ((long long)a.nx * a.ny));
   for (int i = 0; i < kQ3; ++i) {
     const double feq = eq3(a.cs, rho, Ax, Ay, Az, i / 25, (i / 5) % 5, i % 5);
     if (a.state32) {
       const double w = a.cs.w[i / 25] * a.cs.w[(i / 5) % 5] * a.cs.w[i % 5];
-      a.state32[(size_t)i * plane + v] =
+      a.state32[a.lay.at(i, x, y, z)] =
           make_float2((float)(feq - w), a.npop == 2 ? (float)(a.K * theta * feq - a.K * w) : 0.f);
     } else {
       a.state[(size_t)i * plane + v] = feq;
@@ -381,11 +810,12 @@ __global__ void moments3d_kernel(const __grid_constant__ Field3Args a) {
   const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= a.nv) return;
   const size_t plane = (size_t)a.nv;
+  const int x = (int)(v % a.nx), y = (int)((v / a.nx) % a.ny), z = (int)(v / ((long long)a.nx * a.ny));
   double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, e2 = 0.0;
   for (int i = 0; i < kQ3; ++i) {
     double f, g;
     if (a.state32) {
-      const float2 p = a.state32[(size_t)i * plane + v];
+      const float2 p = a.state32[a.lay.at(i, x, y, z)];
       const double w = a.cs.w[i / 25] * a.cs.w[(i / 5) % 5] * a.cs.w[i % 5];
       f = (double)p.x + w;
       g = a.npop == 2 ? (double)p.y + a.K * w : 0.0;
@@ -483,6 +913,11 @@ struct sllbm3d_ctx {
   int* off[3] = {nullptr, nullptr, nullptr};
   float* w32[3] = {nullptr, nullptr, nullptr};
   double* w64[3] = {nullptr, nullptr, nullptr};
+  // sum-factorised FP32 step (orders 1, 2 with an even x count): tail sums per axis, moment sums
+  bool tiled = false;
+  Pad3 lay{};                            // layout of the FP32 pair state
+  float* tail[3] = {nullptr, nullptr, nullptr};
+  float* sums = nullptr;
   int* flag = nullptr;
   std::vector<void*> allocations;
   std::string err;
@@ -516,10 +951,92 @@ sllbm_status alloc3(sllbm3d_ctx* c, T** ptr, size_t count) {
 unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 // storage of one state buffer in 8-byte units: FP64 populations or FP32 (f, g) pairs
-size_t state_doubles(const sllbm3d_ctx* c) { return (size_t)(c->f32 ? 1 : c->npop) * kQ3 * c->nv; }
+size_t state_doubles(const sllbm3d_ctx* c) {
+  return c->f32 ? (size_t)kQ3 * c->lay.plane : (size_t)c->npop * kQ3 * c->nv;
+}
 // doubles of the dense FP64 layout exchanged by get_state / set_state
 size_t dense_doubles(const sllbm3d_ctx* c) { return (size_t)c->npop * kQ3 * c->nv; }
 float2* pairs(const sllbm3d_ctx* c, int k) { return reinterpret_cast<float2*>(c->state[k]); }
+
+// The sum-factorised FP32 step: stream3d_kernel (a CTA per tile) then collide3d_kernel.
+template <int P>
+cudaError_t launch_stream3d(const Stream3Args& a, cudaStream_t s) {
+  using SH = T3Shape<P>;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  // 4D map of the ghost-padded source pairs as floats: (2 x column, row, slice, velocity plane)
+  CUtensorMap smap;
+  const cuuint64_t dims[4] = {(cuuint64_t)2 * a.lay.pitch, (cuuint64_t)a.lay.rows,
+                              (cuuint64_t)(a.lay.plane / ((size_t)a.lay.pitch * a.lay.rows)), (cuuint64_t)kQ3};
+  const cuuint64_t strides[3] = {(cuuint64_t)a.lay.pitch * sizeof(float2),
+                                 (cuuint64_t)a.lay.pitch * a.lay.rows * sizeof(float2),
+                                 (cuuint64_t)a.lay.plane * sizeof(float2)};
+  const cuuint32_t box[4] = {(cuuint32_t)(2 * SH::RX), (cuuint32_t)SH::RY, (cuuint32_t)SH::RZ, 1u};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  if (enc(&smap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float2*>(a.src), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(stream3d_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::kBytes);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (long long)((a.nx + kT3X - 1) / kT3X) * ((a.ny + kT3Y - 1) / kT3Y) * ((a.nz + kT3Z - 1) / kT3Z);
+  stream3d_kernel<P><<<(unsigned)tiles, kT3NT, SH::kBytes, s>>>(a, smap);
+  return cudaGetLastError();
+}
+
+// The periodic images of the current state's ghost cells (after init and set_state).
+cudaError_t fill_ghosts3d(sllbm3d_ctx* c) {
+  if (!c->tiled) return cudaSuccess;
+  const long long n = (long long)kQ3 * (long long)c->lay.plane;
+  ghost3d_kernel<<<blocks_for(n, 256), 256, 0, c->stream>>>(pairs(c, c->cur), c->lay, c->ax.nv, c->ay.nv, c->az.nv,
+                                                           c->ax.periodic, c->ay.periodic, c->az.periodic);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tiled3d(sllbm3d_ctx* c, const float2* src, float2* dst) {
+  Stream3Args a{};
+  a.src = src;
+  a.dst = dst;
+  a.sums = c->sums;
+  a.nx = c->ax.nv;
+  a.ny = c->ay.nv;
+  a.nz = c->az.nv;
+  a.nv = c->nv;
+  a.lay = c->lay;
+  a.tx = c->tail[0];
+  a.ty = c->tail[1];
+  a.tz = c->tail[2];
+  a.cs = c->cs;
+  a.flag = c->flag;
+  cudaError_t e = c->g.order == 1 ? launch_stream3d<1>(a, c->stream) : launch_stream3d<2>(a, c->stream);
+  if (e != cudaSuccess) return e;
+  Collide3Args b{};
+  b.dst = dst;
+  b.lay = c->lay;
+  b.sums = c->sums;
+  b.nx = c->ax.nv;
+  b.ny = c->ay.nv;
+  b.nz = c->az.nv;
+  b.px = c->ax.periodic;
+  b.py = c->ay.periodic;
+  b.pz = c->az.periodic;
+  b.nv = c->nv;
+  b.cs = c->cs;
+  b.omega = (float)(1.0 / c->p.tau);
+  b.K = (float)(2.0 * c->p.cv - 3.0);
+  b.cv = (float)c->p.cv;
+  b.inv2cv = (float)(0.5 / c->p.cv);
+  b.npop = c->npop;
+  b.iso = c->p.isothermal;
+  b.flag = c->flag;
+  collide3d_kernel<<<blocks_for(c->nv, 128), 128, 0, c->stream>>>(b);
+  cudaError_t e2 = cudaGetLastError();
+  if (e2 != cudaSuccess) return e2;
+  const long long per_plane = (long long)c->lay.plane - c->nv;   // ghost cells of a plane
+  ghost_refresh3d_kernel<<<blocks_for((long long)kQ3 * per_plane, 256), 256, 0, c->stream>>>(
+      dst, c->lay, b.nx, b.ny, b.nz, b.px, b.py, b.pz, per_plane);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -556,8 +1073,22 @@ sllbm_status sllbm3d_create(const sllbm_grid3_desc* g, const sllbm_params* p, vo
   c->nv = (long long)c->ax.nv * c->ay.nv * c->az.nv;
   c->npop = p->cv == 1.5 ? 1 : 2;
   c->f32 = p->prec == SLLBM_PREC_F32;
+  // the sum-factorised FP32 step: orders 1, 2, an even x count (16-byte pair rows), and axes at
+  // least as long as its staged region (36 x 12 x 8 vertices); its state keeps ghost cells
+  c->tiled = c->f32 && g->order <= 2 && c->ax.nv % 2 == 0 && c->ax.nv >= T3Shape<2>::RX &&
+             c->ay.nv >= T3Shape<2>::RY && c->az.nv >= T3Shape<2>::RZ && encode_fn() != nullptr;
+  {
+    Pad3& L = c->lay;
+    L.g = c->tiled ? kT3G : 0;
+    L.pitch = c->ax.nv + 2 * L.g;
+    L.rows = c->ay.nv + 2 * L.g;
+    L.plane = (size_t)L.pitch * L.rows * (c->az.nv + 2 * L.g);
+    L.origin = ((size_t)L.g * L.rows + L.g) * L.pitch + L.g;
+  }
   sllbm_status s = SLLBM_OK;
   for (int k = 0; k < 2 && s == SLLBM_OK; ++k) s = alloc3(c, &c->state[k], state_doubles(c));
+  for (int k = 0; k < 2 && s == SLLBM_OK && c->tiled; ++k)   // ghosts of zero-gradient faces stay 0
+    s = cuda3(c, cudaMemsetAsync(c->state[k], 0, state_doubles(c) * sizeof(double), c->stream), "cudaMemsetAsync");
   if (s == SLLBM_OK) s = alloc3(c, &c->flag, 1);
   if (s == SLLBM_OK) s = cuda3(c, cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream), "cudaMemsetAsync");
   if (s != SLLBM_OK) {
@@ -606,6 +1137,26 @@ sllbm_status sllbm3d_precompute_departures(sllbm3d_ctx* c) {
                                                        c->stream), "launch_axis_tables");
     if (s != SLLBM_OK) return s;
   }
+  if (c->tiled) {
+    const int P = c->g.order;
+    for (int k = 0; k < 3; ++k) {
+      const int n = axes[k]->nv;
+      if (!c->tail[k]) {
+        const sllbm_status s = alloc3(c, &c->tail[k], (size_t)kQ1 * n * 2 * P);
+        if (s != SLLBM_OK) return s;
+      }
+      if (P == 1)
+        tail_table_kernel<1><<<blocks_for((long long)kQ1 * n, 128), 128, 0, c->stream>>>(c->off[k], c->w64[k], n, c->tail[k]);
+      else
+        tail_table_kernel<2><<<blocks_for((long long)kQ1 * n, 128), 128, 0, c->stream>>>(c->off[k], c->w64[k], n, c->tail[k]);
+      const sllbm_status s = cuda3(c, cudaGetLastError(), "tail_table_kernel");
+      if (s != SLLBM_OK) return s;
+    }
+    if (!c->sums) {
+      const sllbm_status s = alloc3(c, &c->sums, (size_t)6 * c->nv);
+      if (s != SLLBM_OK) return s;
+    }
+  }
   c->precomputed = true;
   return SLLBM_OK;
 }
@@ -622,13 +1173,17 @@ sllbm_status sllbm3d_init_equilibrium(sllbm3d_ctx* c, const double* rho, const d
   a.T = T;
   a.state = c->state[c->cur];
   a.state32 = c->f32 ? pairs(c, c->cur) : nullptr;
+  a.lay = c->lay;
+  a.nx = c->ax.nv;
+  a.ny = c->ay.nv;
   a.nv = c->nv;
   a.cs = c->cs;
   a.K = 2.0 * c->p.cv - 3.0;
   a.cv = c->p.cv;
   a.npop = c->npop;
   init3d_kernel<<<blocks_for(c->nv, 128), 128, 0, c->stream>>>(a);
-  const sllbm_status s = cuda3(c, cudaGetLastError(), "init3d_kernel");
+  sllbm_status s = cuda3(c, cudaGetLastError(), "init3d_kernel");
+  if (s == SLLBM_OK) s = cuda3(c, fill_ghosts3d(c), "ghost3d_kernel");
   if (s == SLLBM_OK) c->initialized = true;
   return s;
 }
@@ -682,6 +1237,12 @@ sllbm_status sllbm3d_step(sllbm3d_ctx* c, int nsteps) {
     b.iso = a.iso;
     b.flag = a.flag;
     for (int k = 0; k < nsteps; ++k) {
+      if (c->tiled) {
+        const sllbm_status s = cuda3(c, launch_tiled3d(c, pairs(c, c->cur), pairs(c, c->cur ^ 1)), "stream3d/collide3d");
+        if (s != SLLBM_OK) return s;
+        c->cur ^= 1;
+        continue;
+      }
       b.src = pairs(c, c->cur);
       b.dst = pairs(c, c->cur ^ 1);
       switch (c->g.order) {
@@ -712,6 +1273,11 @@ sllbm_status sllbm3d_step(sllbm3d_ctx* c, int nsteps) {
   return SLLBM_OK;
 }
 
+const char* sllbm3d_step_kernel_name(const sllbm3d_ctx* c) {
+  if (!c) return "";
+  return !c->f32 ? "plain_f64" : (c->tiled ? "stream3d" : "gather_f32");
+}
+
 sllbm_status sllbm3d_moments(sllbm3d_ctx* c, double* rho, double* u, double* v, double* w, double* T) {
   if (!c) return SLLBM_ERR_ARG;
   if (!c->initialized) return fail3(c, SLLBM_ERR_STATE, "init first");
@@ -723,6 +1289,9 @@ sllbm_status sllbm3d_moments(sllbm3d_ctx* c, double* rho, double* u, double* v, 
   a.oT = T;
   a.state = c->state[c->cur];
   a.state32 = c->f32 ? pairs(c, c->cur) : nullptr;
+  a.lay = c->lay;
+  a.nx = c->ax.nv;
+  a.ny = c->ay.nv;
   a.nv = c->nv;
   a.cs = c->cs;
   a.K = 2.0 * c->p.cv - 3.0;
@@ -736,6 +1305,7 @@ sllbm_status sllbm3d_moments(sllbm3d_ctx* c, double* rho, double* u, double* v, 
   s = cuda3(c, cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
   if (s == SLLBM_OK) s = cuda3(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
   if (s != SLLBM_OK) return s;
+  if (flag & 4) return fail3(c, SLLBM_ERR_CUDA, "a staging copy of the 3D stream kernel timed out");
   return (flag & 1) ? fail3(c, SLLBM_ERR_UNSTABLE, "non-positive or non-finite density or temperature") : SLLBM_OK;
 }
 
@@ -743,7 +1313,7 @@ sllbm_status sllbm3d_get_state(sllbm3d_ctx* c, double* dst) {
   if (!c || !dst) return fail3(c, SLLBM_ERR_ARG, "null pointer");
   if (c->f32) {
     convert3d_kernel<<<blocks_for((long long)kQ3 * c->nv, 256), 256, 0, c->stream>>>(
-        pairs(c, c->cur), dst, c->nv, c->npop, 2.0 * c->p.cv - 3.0, c->cs, 1);
+        pairs(c, c->cur), c->lay, dst, c->ax.nv, c->ay.nv, c->nv, c->npop, 2.0 * c->p.cv - 3.0, c->cs, 1);
     return cuda3(c, cudaGetLastError(), "convert3d_kernel");
   }
   return cuda3(c, cudaMemcpyAsync(dst, c->state[c->cur], state_doubles(c) * sizeof(double), cudaMemcpyDeviceToDevice,
@@ -754,8 +1324,10 @@ sllbm_status sllbm3d_set_state(sllbm3d_ctx* c, const double* src) {
   if (!c || !src) return fail3(c, SLLBM_ERR_ARG, "null pointer");
   if (c->f32) {
     convert3d_kernel<<<blocks_for((long long)kQ3 * c->nv, 256), 256, 0, c->stream>>>(
-        pairs(c, c->cur), const_cast<double*>(src), c->nv, c->npop, 2.0 * c->p.cv - 3.0, c->cs, 0);
-    const sllbm_status s = cuda3(c, cudaGetLastError(), "convert3d_kernel");
+        pairs(c, c->cur), c->lay, const_cast<double*>(src), c->ax.nv, c->ay.nv, c->nv, c->npop,
+        2.0 * c->p.cv - 3.0, c->cs, 0);
+    sllbm_status s = cuda3(c, cudaGetLastError(), "convert3d_kernel");
+    if (s == SLLBM_OK) s = cuda3(c, fill_ghosts3d(c), "ghost3d_kernel");
     if (s == SLLBM_OK) c->initialized = true;
     return s;
   }

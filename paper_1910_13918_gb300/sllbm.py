@@ -33,7 +33,7 @@ EXPORTS = [
     "sllbm_selftest_bounded_wait",
     "sllbm3d_create", "sllbm3d_destroy", "sllbm3d_grid_info", "sllbm3d_vertex_coords",
     "sllbm3d_precompute_departures", "sllbm3d_init_equilibrium", "sllbm3d_step", "sllbm3d_moments",
-    "sllbm3d_get_state", "sllbm3d_set_state", "sllbm3d_last_error",
+    "sllbm3d_get_state", "sllbm3d_set_state", "sllbm3d_last_error", "sllbm3d_step_kernel_name",
 ]
 
 
@@ -113,6 +113,7 @@ def load(path: str | None = None):
         "sllbm3d_get_state": ([P, V], I),
         "sllbm3d_set_state": ([P, V], I),
         "sllbm3d_last_error": ([P], ctypes.c_char_p),
+        "sllbm3d_step_kernel_name": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -290,7 +291,8 @@ class SLLBM:
 
 class SLLBM3D:
     """The 3D extension (D3Q125, hexahedral cells) on the current CUDA device: the plain FP64 step
-    (``prec="f64"``) or the fused FP32 step on deviation pairs (``prec="f32"``)."""
+    (``prec="f64"``) or an FP32 step on deviation pairs (``prec="f32"``: sum-factorised and
+    TMA-staged where the grid allows, else the one-launch gather step)."""
 
     def __init__(self, *, cells, order, box, bc, dt, tau, cv, isothermal=False,
                  nodes=NODES_GLC, prec="f64", stream=None):
@@ -343,6 +345,11 @@ class SLLBM3D:
 
     def precompute(self):
         self._check(self.lib.sllbm3d_precompute_departures(self.h))
+
+    @property
+    def kernel_name(self):
+        """The kernel sllbm3d_step uses: "stream3d", "gather_f32" or "plain_f64"."""
+        return self.lib.sllbm3d_step_kernel_name(self.h).decode()
 
     def init(self, rho, u, v, w, T):
         ts = [self.torch.as_tensor(a, dtype=self.torch.float64, device=self.device).contiguous()

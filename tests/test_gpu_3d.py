@@ -20,6 +20,17 @@ CASES = {
     "isothermal_p2": ((2, 2, 1), 2, ((0.0, 1.0), (0.0, 1.0), (0.0, 0.5)), True, 0.015, 0.9, 1.5, True, 3),
 }
 
+# Grids the sum-factorised FP32 step takes (tiles of 32 x 8 x 4 vertices; x vertex count even, at
+# least 36 x 12 x 8): ragged tiles on every axis, periodic faces (regions reaching the periodic
+# images in the ghost cells) and zero-gradient ones, orders 1 and 2, two populations and the
+# isothermal single population.
+TILED = {
+    "tiled_periodic_p2": ((20, 7, 5), 2, ((0.0, 1.0), (0.0, 0.35), (0.0, 0.25)), True, 0.002, 0.8, 2.5, False, 3),
+    "tiled_periodic_p1": ((38, 13, 9), 1, ((0.0, 1.0), (0.0, 0.35), (0.0, 0.25)), True, 0.003, 0.7, 2.5, False, 3),
+    "tiled_clamped_p1": ((37, 12, 8), 1, ((0.0, 1.0), (0.0, 0.3), (0.0, 0.2)), False, 0.003, 0.9, 2.5, False, 3),
+    "tiled_isothermal_p2": ((18, 6, 4), 2, ((0.0, 1.0), (0.0, 0.35), (0.0, 0.22)), True, 0.002, 0.9, 1.5, True, 3),
+}
+
 
 def _fields(X, Y, Z, box, seed):
     (x0, x1), (y0, y1), (z0, z1) = box
@@ -86,13 +97,15 @@ def test_3d_state_round_trip(gpu_lib):
     assert np.array_equal(s.get_state().cpu().numpy(), after.cpu().numpy())
 
 
-@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("name", list(CASES) + list(TILED))
 def test_3d_fused_f32_step_against_oracle(gpu_lib, name):
-    """The fused FP32 step (deviation pairs, one launch a step): rho, u, v, w, T after the case's
-    steps within the FP32 tolerance of the 2D step (1e-5, velocities relative to the flow's
-    scale), and populations to FP32 precision of the deviations (3e-5 of their largest value)."""
-    case = CASES[name]
+    """The FP32 steps (deviation pairs): the one-launch gather step on the small grids, the
+    sum-factorised step on the TILED ones.  rho, u, v, w, T after the case's steps within the FP32
+    tolerance of the 2D step (1e-5, velocities relative to the flow's scale), and populations to
+    FP32 precision of the deviations (3e-5 of their largest value)."""
+    case = {**CASES, **TILED}[name]
     s = _gpu(case, "f32")
+    assert s.kernel_name == ("stream3d" if name in TILED else "gather_f32"), s.kernel_name
     f, g = _oracle(case)
     st = s.get_state().cpu().numpy()
     xi, w = o3.d3q125()
@@ -106,6 +119,22 @@ def test_3d_fused_f32_step_against_oracle(gpu_lib, name):
     assert np.max(np.abs(m["T"].cpu().numpy() / th - 1)) < 1e-5
     for k, name_ in enumerate(("u", "v", "w")):
         assert np.max(np.abs(m[name_].cpu().numpy() - u[..., k])) < 1e-5 * umax, name_
+
+
+def test_3d_tiled_f32_tracks_f64_over_10_steps(gpu_lib):
+    """The sum-factorised FP32 step against the plain FP64 step over 10 steps on the ragged
+    periodic p = 2 grid: both populations within the multi-step FP32 tolerance (1e-4 of the
+    largest deviation of each population; one step's rounding is a few 1e-6 of it)."""
+    case = TILED["tiled_periodic_p2"][:-1] + (10,)
+    s32, s64 = _gpu(case, "f32"), _gpu(case, "f64")
+    assert s32.kernel_name == "stream3d" and s64.kernel_name == "plain_f64"
+    a, b = s32.get_state().cpu().numpy(), s64.get_state().cpu().numpy()
+    xi, w = o3.d3q125()
+    K = 2 * case[6] - 3
+    for pop, ref in ((0, w), (1, K * w)):
+        scale = np.max(np.abs(b[pop] - ref[:, None, None, None]))
+        err = np.max(np.abs(a[pop] - b[pop]))
+        assert err <= 1e-4 * scale, (pop, err / scale)
 
 
 def test_3d_fused_f32_keeps_mass_and_energy_of_f64(gpu_lib):
