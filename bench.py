@@ -42,12 +42,12 @@ SECONDARY = "tgv256"          # second grid of the line: the Taylor-Green vortex
 # DRAM traffic (read + write bytes per launch) of the step kernel from an ncu capture, keyed by
 # (kernel source digest, workload, precision); reported as null once the kernel source changes.
 NCU_TRAFFIC = {
-    # 512^2-cell capture: 516.6 MB read + 429.1 MB written for 2,362,369 vertices, scaled by the
+    # 512^2-cell capture: 512.9 MB read + 428.8 MB written for 2,362,369 vertices, scaled by the
     # vertex count to the 3073^2 grid (a multi-pass capture of that grid exceeds the size rule)
-    ("19f47ef50d49815d", "riemann1024_p3_tableIII", "f32"): 945.69e6 * 9443329 / 2362369,
-    ("19f47ef50d49815d", "riemann512_p3_tableIII", "f32"): 945.69e6,
-    # full-size capture: 219.3 MB read + 174.6 MB written
-    ("19f47ef50d49815d", "tgv256_p4", "f32"): 393.84e6,
+    ("fbe8df125e8dee04", "riemann1024_p3_tableIII", "f32"): 941.77e6 * 9443329 / 2362369,
+    ("fbe8df125e8dee04", "riemann512_p3_tableIII", "f32"): 941.77e6,
+    # full-size capture: 220.1 MB read + 174.2 MB written
+    ("fbe8df125e8dee04", "tgv256_p4", "f32"): 394.28e6,
 }
 
 # Sources that decide what the fused kernels of NCU_TRAFFIC do and how they are launched on
@@ -572,7 +572,8 @@ def adjoint_time(s, stream, ws, updates):
         torch.cuda.synchronize()
     ms = max_over_ranks(a0.elapsed_time(a1)) / ka
     return {"ms_per_step": ms, "value": updates * ws / (ms * 1e-3) / 1e9, "unit": UNIT, "steps": ka,
-            "note": "sllbm_adjoint_step: pointwise J_C^T, then S^T as a pull over transposed stencils"}
+            "note": "sllbm_adjoint_step: pointwise J_C^T into ghost-padded pairs, then S^T as a pull "
+                    "over transposed stencils (TMA-staged on uniform grids)"}
 
 
 def e2e_time(s, args, ws, updates):
