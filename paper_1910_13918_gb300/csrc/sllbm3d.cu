@@ -187,10 +187,6 @@ __device__ __forceinline__ int wrap1(int j, int n, int periodic) {
   return j < 0 ? j + n : (j >= n ? j - n : j);
 }
 
-// Weight w_abc of velocity i = 25a + 5b + c (FP32).
-__device__ __forceinline__ float w3f(const Consts& cs, int i) {
-  return cs.wf[i / 25] * cs.wf[(i / 5) % 5] * cs.wf[i % 5];
-}
 
 // Fused FP32 step, one thread per vertex, one launch.  First sweep: every velocity's (f, g) pair
 // is interpolated at its departure point (tensor product of the three 1D Lagrange bases, each in
@@ -954,8 +950,6 @@ unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads -
 size_t state_doubles(const sllbm3d_ctx* c) {
   return c->f32 ? (size_t)kQ3 * c->lay.plane : (size_t)c->npop * kQ3 * c->nv;
 }
-// doubles of the dense FP64 layout exchanged by get_state / set_state
-size_t dense_doubles(const sllbm3d_ctx* c) { return (size_t)c->npop * kQ3 * c->nv; }
 float2* pairs(const sllbm3d_ctx* c, int k) { return reinterpret_cast<float2*>(c->state[k]); }
 
 // The sum-factorised FP32 step: stream3d_kernel (a CTA per tile) then collide3d_kernel.
