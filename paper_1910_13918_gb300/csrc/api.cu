@@ -504,12 +504,28 @@ static cudaError_t convert_state(sllbm_ctx* c, const void* src, void* dst, bool 
                               c->plane_stride, c->xs, c->ps, c->stream);
 }
 
+// Interleaved (f, g) pairs convert by velocity plane, both populations at once.
+static bool pair_layout(const sllbm_ctx* c) { return c->xs == 2 && c->ps == 1 && c->ny <= 65535; }
+
+static cudaError_t convert_pairs(sllbm_ctx* c, const void* src, void* dst, bool to_internal, int i0, int ni) {
+  return launch_pair_convert(src, dst, to_internal, c->elem, i0, ni, c->npop, c->nq, c->nx, c->ny, c->pitch,
+                             c->plane_stride, c->stream);
+}
+
 static size_t dense_bytes(const sllbm_ctx* c) { return (size_t)c->npop * c->nq * c->nv * c->elem; }
 
+// Dense [npop][nq][ny][nx] state (host or device) <-> the internal layout.  Host transfers go in
+// kXferChunks groups of planes on a copy stream, each group's conversion on the compute stream
+// overlapping the next group's copy.  With (f, g) pairs a group is a range of velocity planes
+// with both populations (one copy per population), converted pair by pair.
 static sllbm_status copy_state(sllbm_ctx* c, void* dst, const void* src, bool to_internal, cudaMemcpyKind kind) {
+  const bool pairs = pair_layout(c);
   const int planes = c->npop * c->nq;
   if (kind == cudaMemcpyDeviceToDevice) {
-    CUDA_TRY(c, convert_state(c, src, dst, to_internal, 0, planes));
+    if (pairs)
+      CUDA_TRY(c, convert_pairs(c, src, dst, to_internal, 0, c->nq));
+    else
+      CUDA_TRY(c, convert_state(c, src, dst, to_internal, 0, planes));
     return SLLBM_OK;
   }
   if (!c->dense) {
@@ -522,30 +538,40 @@ static sllbm_status copy_state(sllbm_ctx* c, void* dst, const void* src, bool to
     for (int k = 0; k <= kXferChunks; ++k) CUDA_TRY(c, cudaEventCreateWithFlags(&c->xev[k], cudaEventDisableTiming));
   }
   const size_t plane_bytes = (size_t)c->nv * c->elem;
-  auto chunk = [&](int k, int* p0, int* np) {
-    *p0 = planes * k / kXferChunks;
-    *np = planes * (k + 1) / kXferChunks - *p0;
-  };
+  const int units = pairs ? c->nq : planes;   // chunked unit: velocity plane (pairs) or dense plane
+  const int copies = pairs ? c->npop : 1;     // host copies per chunk
+  const size_t pop_bytes = (size_t)c->nq * plane_bytes;
   // the copy stream starts after the work already queued on the compute stream
   CUDA_TRY(c, cudaEventRecord(c->xev[kXferChunks], c->stream));
   CUDA_TRY(c, cudaStreamWaitEvent(c->xfer, c->xev[kXferChunks], 0));
   char* dense = static_cast<char*>(c->dense);
   for (int k = 0; k < kXferChunks; ++k) {
-    int p0, np;
-    chunk(k, &p0, &np);
+    const int p0 = units * k / kXferChunks, np = units * (k + 1) / kXferChunks - p0;
     if (np == 0) continue;
     if (to_internal) {
-      CUDA_TRY(c, cudaMemcpyAsync(dense + p0 * plane_bytes, static_cast<const char*>(src) + p0 * plane_bytes,
-                                  np * plane_bytes, cudaMemcpyHostToDevice, c->xfer));
+      for (int q = 0; q < copies; ++q) {
+        const size_t off = q * pop_bytes + p0 * plane_bytes;
+        CUDA_TRY(c, cudaMemcpyAsync(dense + off, static_cast<const char*>(src) + off, np * plane_bytes,
+                                    cudaMemcpyHostToDevice, c->xfer));
+      }
       CUDA_TRY(c, cudaEventRecord(c->xev[k], c->xfer));
       CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->xev[k], 0));
-      CUDA_TRY(c, convert_state(c, dense, dst, true, p0, np));
+      if (pairs)
+        CUDA_TRY(c, convert_pairs(c, dense, dst, true, p0, np));
+      else
+        CUDA_TRY(c, convert_state(c, dense, dst, true, p0, np));
     } else {
-      CUDA_TRY(c, convert_state(c, src, dense, false, p0, np));
+      if (pairs)
+        CUDA_TRY(c, convert_pairs(c, src, dense, false, p0, np));
+      else
+        CUDA_TRY(c, convert_state(c, src, dense, false, p0, np));
       CUDA_TRY(c, cudaEventRecord(c->xev[k], c->stream));
       CUDA_TRY(c, cudaStreamWaitEvent(c->xfer, c->xev[k], 0));
-      CUDA_TRY(c, cudaMemcpyAsync(static_cast<char*>(dst) + p0 * plane_bytes, dense + p0 * plane_bytes,
-                                  np * plane_bytes, cudaMemcpyDeviceToHost, c->xfer));
+      for (int q = 0; q < copies; ++q) {
+        const size_t off = q * pop_bytes + p0 * plane_bytes;
+        CUDA_TRY(c, cudaMemcpyAsync(static_cast<char*>(dst) + off, dense + off, np * plane_bytes,
+                                    cudaMemcpyDeviceToHost, c->xfer));
+      }
     }
   }
   // the compute stream resumes after the last copy (so that synchronising it covers the transfer,

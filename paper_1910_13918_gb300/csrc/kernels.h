@@ -136,6 +136,10 @@ cudaError_t launch_init_equilibrium(const InitArgs& a, cudaStream_t s);
 cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int plane0,
                                  int nplanes, int nq, int nx, int ny, int pitch, size_t plane_stride,
                                  int xs, ptrdiff_t ps, cudaStream_t s);
+// Dense [npop][nq][ny][nx] <-> interleaved (f, g) pairs (xs = 2, ps = 1) for the velocity planes
+// [i0, i0 + ni), both populations at once (elem 4: FP32, 2: BF16).
+cudaError_t launch_pair_convert(const void* src, void* dst, bool to_internal, int elem, int i0, int ni, int npop,
+                                int nq, int nx, int ny, int pitch, size_t plane_stride, cudaStream_t s);
 // Copy the periodic images of interior vertices into the ghost cells of `planes` planes (clamped
 // copies on non-periodic axes).  `origin`: interior origin of plane 0; elem: bytes per element.
 cudaError_t launch_ghost_fill(void* origin, int elem, size_t plane_stride, int pitch, int planes,

@@ -342,6 +342,46 @@ __global__ void state_convert_kernel(const E* src, E* dst, int to_internal, int 
     dst[t] = src[o];
 }
 
+// Dense [npop][nq][ny][nx] <-> interleaved (f, g) pairs (xs = 2, ps = 1) for the velocity planes
+// i0 .. i0 + gridDim.z - 1: one thread per (plane, vertex), f and g together, so that a pair moves
+// as one 8-byte (FP32) or 4-byte (BF16) access (g = 0 with one population).
+template <typename E, typename E2>
+__global__ void pair_convert_kernel(const E* src, E* dst, int to_internal, int i0, int npop, int nq, int nx,
+                                    int ny, int pitch, size_t plane_stride) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, i = i0 + blockIdx.z;
+  if (x >= nx) return;
+  const size_t nv = (size_t)nx * ny;
+  const size_t d = ((size_t)i * ny + y) * nx + x;                            // f in the dense layout
+  const size_t o = (size_t)i * plane_stride + (size_t)y * pitch + 2 * (size_t)x;   // the pair
+  if (to_internal) {
+    E2 p;
+    p.x = src[d];
+    p.y = npop == 2 ? src[(size_t)nq * nv + d] : E(0);
+    *reinterpret_cast<E2*>(dst + o) = p;
+  } else {
+    const E2 p = *reinterpret_cast<const E2*>(src + o);
+    dst[d] = p.x;
+    if (npop == 2) dst[(size_t)nq * nv + d] = p.y;
+  }
+}
+
+cudaError_t launch_pair_convert(const void* src, void* dst, bool to_internal, int elem, int i0, int ni, int npop,
+                                int nq, int nx, int ny, int pitch, size_t plane_stride, cudaStream_t s) {
+  if (ni == 0) return cudaSuccess;
+  if (ny > 65535 || ni > 65535) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((nx + 255) / 256), (unsigned)ny, (unsigned)ni);
+  const int ti = to_internal ? 1 : 0;
+  if (elem == 4)
+    pair_convert_kernel<uint32_t, uint2><<<grid, 256, 0, s>>>(static_cast<const uint32_t*>(src),
+        static_cast<uint32_t*>(dst), ti, i0, npop, nq, nx, ny, pitch, plane_stride);
+  else if (elem == 2)
+    pair_convert_kernel<uint16_t, ushort2><<<grid, 256, 0, s>>>(static_cast<const uint16_t*>(src),
+        static_cast<uint16_t*>(dst), ti, i0, npop, nq, nx, ny, pitch, plane_stride);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_state_convert(const void* src, void* dst, bool to_internal, int elem, int plane0,
                                  int nplanes, int nq, int nx, int ny, int pitch, size_t plane_stride,
                                  int xs, ptrdiff_t ps, cudaStream_t s) {
