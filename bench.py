@@ -407,7 +407,13 @@ def measure(w, prec, args, stream, verts, sampler=None, keep=False):
     from paper_1910_13918_gb300.sllbm import SLLBM
     with torch.cuda.stream(stream):
         s = SLLBM.from_workload(w, prec=prec, stream=stream)
-        s.precompute()
+        p0, p1 = _event_pair()
+        torch.cuda.synchronize()
+        p0.record(stream)
+        s.precompute()   # departure tables / descriptors and vertex weights, FP64
+        p1.record(stream)
+        torch.cuda.synchronize()
+        precompute_ms = p0.elapsed_time(p1)
         x, y = (t.cpu().numpy() for t in s.coords())
         s.init(*w.fields(x, y))
         del x, y
@@ -433,10 +439,23 @@ def measure(w, prec, args, stream, verts, sampler=None, keep=False):
             _barrier()
             ms.append(max_over_ranks(e0.elapsed_time(e1)))
         clocks = sampler.stop() if sampler else None
+        with_moments = None
+        if keep:   # the same steps with the moments epilogue (16 B more a vertex), after the above
+            buf = torch.empty((4, s.ny, s.nx), dtype=torch.float32, device=s.device)
+            e0, e1 = _event_pair()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                s.step_moments(buf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            with_moments = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+            del buf
         mom = s.moments()
         final = torch.stack([mom["rho"], mom["u"], mom["v"], mom["T"]])
         info = {"kernel": s.kernel_name, "launches_per_step": s.launches_per_step,
-                "state_bytes": s.state_bytes, "mass_after": mom["mass"], "nx": s.nx, "ny": s.ny}
+                "state_bytes": s.state_bytes, "mass_after": mom["mass"], "nx": s.nx, "ny": s.ny,
+                "precompute_ms": precompute_ms, "ms_per_step_with_moments": with_moments}
     if not keep:
         s.close()
         s = None
@@ -457,12 +476,19 @@ def _summary(w, prec, r, args, ws, peak):
     upd = w.updates_per_step
     alg = upd * bytes_per_update(w, prec, r["info"]["kernel"])
     achieved = alg / (ms_step * 1e-3) / 1e9
-    return {"ms_per_step": ms_step, "value": upd * ws / (ms_step * 1e-3) / 1e9, "unit": UNIT,
-            "kernel": r["info"]["kernel"], "launches_per_step": r["info"]["launches_per_step"],
-            "ms_per_region_repeats": r["ms"],
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak,
-                         "bytes_per_update": bytes_per_update(w, prec, r["info"]["kernel"])}}
+    out = {"ms_per_step": ms_step, "value": upd * ws / (ms_step * 1e-3) / 1e9, "unit": UNIT,
+           "kernel": r["info"]["kernel"], "launches_per_step": r["info"]["launches_per_step"],
+           "ms_per_region_repeats": r["ms"], "precompute_ms": r["info"]["precompute_ms"],
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak,
+                        "bytes_per_update": bytes_per_update(w, prec, r["info"]["kernel"])}}
+    wm = r["info"]["ms_per_step_with_moments"]
+    if wm:
+        out["with_moments_epilogue"] = {"ms_per_step": wm, "value": upd * ws / (wm * 1e-3) / 1e9,
+                                        "unit": UNIT, "steps": args.steps,
+                                        "note": "sllbm_step_moments: the step plus (rho, u, v, theta) "
+                                                "of every vertex, 16 B a vertex more"}
+    return out
 
 
 def measure_grid(w, args, stream, ws, peak, sampler=None, precs=("f64", "f32", "bf16"), keep="f32"):
