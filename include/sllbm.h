@@ -142,7 +142,11 @@ sllbm_status sllbm_init_equilibrium(sllbm_ctx* ctx, const double* rho_dev, const
 /* Advance nsteps time steps: per step and vertex, interpolate the post-collision populations of
  * every velocity at its departure point (Eq. sl_streaming), take the moments (rho, rho u,
  * 2 rho E of Sec. II), relax toward the equilibrium with 1/tau (Eq. streaming_fg, Pr = 1) and
- * store the post-collision populations.  Enqueues only; returns without synchronising. */
+ * store the post-collision populations.  Enqueues only; returns without synchronising.  On grids
+ * whose state (sllbm_state_bytes) is at most 64 MB, small enough for L2 and bound by launch
+ * overhead, a call of 4 or more steps on a stream other than the legacy default stream replays
+ * pairs of steps as a CUDA graph, captured at the first such call (the same launches with the
+ * same parameters; the result is the same bit for bit). */
 sllbm_status sllbm_step(sllbm_ctx* ctx, int nsteps);
 
 /* One step as sllbm_step that also writes, per vertex, the moments its collision was evaluated
