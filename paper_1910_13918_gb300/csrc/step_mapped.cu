@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kMNT, 2) step_mapped_kernel(const __grid_const
       // out, every thread stops together after the copies in flight for the next stages
       if (__syncthreads_or(late)) {
         const long last = s0 + (long)kQ1 * ((ntiles - tile + (int)gridDim.x - 1) / (int)gridDim.x);
-        for (long t = s + 1; t < s + PD && t < last; ++t)
+        for (long t = s; t < s + PD && t < last; ++t)   // stage s itself and the ones after it
           if (!mbar_wait(&BAR[t % NSB], (unsigned)((t / NSB) & 1), a.flag)) break;
         return;
       }

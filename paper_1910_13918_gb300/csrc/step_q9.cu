@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(kNT) step_q9_tma_kernel(const __grid_constant_
       // wait ran out, every thread stops together after the copies still in flight
       const bool late = (i % 3 == 0) && !mbar_wait(&BAR[buf * kQ9Groups + i / 3], parity, a.flag);
       if (__syncthreads_or(late)) {
-        for (int g = i / 3 + 1; g < kQ9Groups; ++g)   // this tile's later groups
+        for (int g = i / 3; g < kQ9Groups; ++g)   // this group (it may still land) and the later ones
           if (!mbar_wait(&BAR[buf * kQ9Groups + g], parity, a.flag)) return;
         if (k + 1 < my_tiles)                          // the next tile's groups
           for (int g = 0; g < kQ9Groups; ++g)

@@ -284,9 +284,10 @@ __global__ void __launch_bounds__(TileShape<P>::NT, TileShape<P>::MINB)
       const int s = kQ1 * k + j;
       const bool late = ycur && !mbar_wait(&BAR[s % NSB], (unsigned)((s / NSB) & 1), a.flag);
       // stage landed (or its wait ran out: then every thread stops together, after the copies
-      // still in flight for the next stages -- issued up to s + PD - 1 -- have landed)
+      // still in flight -- stage s and the next stages, issued up to s + PD - 1 -- have landed)
       if (__syncthreads_or(late)) {   // also: T[(s-1)&1] written; T[s&1], S[(s+PD)%NSB] free
-        for (int t = s + 1; t < s + PD && t < kQ1 * my_tiles; ++t)
+        // the copies in flight: stage s itself (it may still land) and the ones issued after it
+        for (int t = s; t < s + PD && t < kQ1 * my_tiles; ++t)
           if (!mbar_wait(&BAR[t % NSB], (unsigned)((t / NSB) & 1), a.flag)) break;
         return;
       }
