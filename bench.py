@@ -42,12 +42,12 @@ SECONDARY = "tgv256"          # second grid of the line: the Taylor-Green vortex
 # DRAM traffic (read + write bytes per launch) of the step kernel from an ncu capture, keyed by
 # (kernel source digest, workload, precision); reported as null once the kernel source changes.
 NCU_TRAFFIC = {
-    # 512^2-cell capture: 512.9 MB read + 428.8 MB written for 2,362,369 vertices, scaled by the
+    # 512^2-cell capture: 512.5 MB read + 429.2 MB written for 2,362,369 vertices, scaled by the
     # vertex count to the 3073^2 grid (a multi-pass capture of that grid exceeds the size rule)
-    ("fbe8df125e8dee04", "riemann1024_p3_tableIII", "f32"): 941.77e6 * 9443329 / 2362369,
-    ("fbe8df125e8dee04", "riemann512_p3_tableIII", "f32"): 941.77e6,
-    # full-size capture: 220.1 MB read + 174.2 MB written
-    ("fbe8df125e8dee04", "tgv256_p4", "f32"): 394.28e6,
+    ("1cfc30b07f92dc76", "riemann1024_p3_tableIII", "f32"): 941.67e6 * 9443329 / 2362369,
+    ("1cfc30b07f92dc76", "riemann512_p3_tableIII", "f32"): 941.67e6,
+    # full-size capture: 219.8 MB read + 174.5 MB written
+    ("1cfc30b07f92dc76", "tgv256_p4", "f32"): 394.23e6,
 }
 
 # Sources that decide what the fused kernels of NCU_TRAFFIC do and how they are launched on
