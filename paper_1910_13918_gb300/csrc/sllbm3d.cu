@@ -490,15 +490,32 @@ __global__ void __launch_bounds__(kT3NT, 2) stream3d_kernel(const __grid_constan
     }
     const float2* Sst = S + (size_t)st * RE;
     // z pass: column (ry, rx) of the region, the tile's z rows
-    const float* wz = Wz + ic * kT3Z * NW;
-    for (int t = tid; t < SH::ZT; t += kT3NT) {
-      float2 v[RZ], d[RZ - 1];
+    {
+      // the plane's z tail sums in registers; a thread's (up to) ZR columns with all loads in flight
+      constexpr int ZR = (SH::ZT + kT3NT - 1) / kT3NT;
+      float wz[kT3Z * NW];
 #pragma unroll
-      for (int r = 0; r < RZ; ++r) v[r] = Sst[r * RY * RX + t];
+      for (int q = 0; q < kT3Z * NW; ++q) wz[q] = Wz[ic * kT3Z * NW + q];
+      float2 v[ZR][RZ];
 #pragma unroll
-      for (int r = 0; r + 1 < RZ; ++r) d[r] = sub2(v[r + 1], v[r]);
+      for (int c = 0; c < ZR; ++c) {
+        const int t = tid + c * kT3NT;
+        if (t < SH::ZT) {
 #pragma unroll
-      for (int tz = 0; tz < kT3Z; ++tz) Zb[tz * RY * RX + t] = tail_interp<P>(v, d, tz + P, wz + tz * NW);
+          for (int r = 0; r < RZ; ++r) v[c][r] = Sst[r * RY * RX + t];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < ZR; ++c) {
+        const int t = tid + c * kT3NT;
+        if (t < SH::ZT) {
+          float2 d[RZ - 1];
+#pragma unroll
+          for (int r = 0; r + 1 < RZ; ++r) d[r] = sub2(v[c][r + 1], v[c][r]);
+#pragma unroll
+          for (int tz = 0; tz < kT3Z; ++tz) Zb[tz * RY * RX + t] = tail_interp<P>(v[c], d, tz + P, wz + tz * NW);
+        }
+      }
     }
     __syncthreads();
     // y pass: column (tz, rx), the tile's y rows
