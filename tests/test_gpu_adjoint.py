@@ -24,17 +24,20 @@ def _small_cases():
             "sod_uniform": H.small_workloads()["sod"],
             # several 32 x 32 tiles of the one-pass S^T with ragged edges, clamped on both axes
             "riemann_uniform": W.riemann_paper().resized(14, 12, keep_tau=True),
-            # 16 times the CFL time step: departure points about 8 nodes away, beyond the halo of
-            # the one-pass S^T, so the adjoint takes the two-pass S^T over the (f, g) pairs
-            "tgv_far_uniform": _far(W.tgv256().resized(6, 5))}
+            # 4 times the CFL time step: transposed-stencil halo 5 (over 4), the one-pass S^T
+            # compiled for halo 8
+            "tgv_mid_uniform": _far(W.tgv256().resized(6, 5), 4.0),
+            # 16 times the CFL time step: departure points about 8 nodes away, halo 9, beyond the
+            # one-pass S^T, so the adjoint takes the two-pass S^T over the (f, g) pairs
+            "tgv_far_uniform": _far(W.tgv256().resized(6, 5), 16.0)}
 
 
-def _far(w):
-    return w.resized(w.nx_cells, w.ny_cells, steps=w.steps, dt=16.0 * W.cfl_dt(w))
+def _far(w, factor):
+    return w.resized(w.nx_cells, w.ny_cells, steps=w.steps, dt=factor * W.cfl_dt(w))
 
 
 @pytest.mark.parametrize("name", ["svi_mapped", "tgv_uniform", "sod_uniform", "riemann_uniform",
-                                  "tgv_far_uniform"])
+                                  "tgv_mid_uniform", "tgv_far_uniform"])
 def test_adjoint_step_matches_oracle(gpu_lib, name):
     from paper_1910_13918_gb300.sllbm import SLLBM
     w = _small_cases()[name]
