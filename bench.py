@@ -42,12 +42,12 @@ SECONDARY = "tgv256"          # second grid of the line: the Taylor-Green vortex
 # DRAM traffic (read + write bytes per launch) of the step kernel from an ncu capture, keyed by
 # (kernel source digest, workload, precision); reported as null once the kernel source changes.
 NCU_TRAFFIC = {
-    # 512^2-cell capture: 512.5 MB read + 429.2 MB written for 2,362,369 vertices, scaled by the
+    # 512^2-cell capture: 511.6 MB read + 429.2 MB written for 2,362,369 vertices, scaled by the
     # vertex count to the 3073^2 grid (a multi-pass capture of that grid exceeds the size rule)
-    ("1cfc30b07f92dc76", "riemann1024_p3_tableIII", "f32"): 941.67e6 * 9443329 / 2362369,
-    ("1cfc30b07f92dc76", "riemann512_p3_tableIII", "f32"): 941.67e6,
-    # full-size capture: 219.8 MB read + 174.5 MB written
-    ("1cfc30b07f92dc76", "tgv256_p4", "f32"): 394.23e6,
+    ("99a5f9bcc84ce154", "riemann1024_p3_tableIII", "f32"): 940.84e6 * 9443329 / 2362369,
+    ("99a5f9bcc84ce154", "riemann512_p3_tableIII", "f32"): 940.84e6,
+    # full-size capture: 219.5 MB read + 174.1 MB written
+    ("99a5f9bcc84ce154", "tgv256_p4", "f32"): 393.62e6,
 }
 
 # Sources that decide what the fused kernels of NCU_TRAFFIC do and how they are launched on
@@ -440,7 +440,7 @@ def measure(w, prec, args, stream, verts, sampler=None, keep=False):
             ms.append(max_over_ranks(e0.elapsed_time(e1)))
         clocks = sampler.stop() if sampler else None
         with_moments = None
-        if keep:   # the same steps with the moments epilogue (16 B more a vertex), after the above
+        if keep and w.velset != "d2q9":   # the same steps with the moments epilogue (D2Q25; 16 B a vertex)
             buf = torch.empty((4, s.ny, s.nx), dtype=torch.float32, device=s.device)
             e0, e1 = _event_pair()
             torch.cuda.synchronize()

@@ -55,7 +55,7 @@ struct sllbm_ctx {
   int cur = 0;
   bool precomputed = false, initialized = false;
   int kernel = kKernelGather;
-  int q9_tma = 0;                        // D2Q9 FP32 uniform: the TMA-staged kernel
+  int q9_tma = 0;                        // D2Q9 FP32/BF16 uniform: the TMA-staged kernel
   // uniform tables
   int *offx = nullptr, *offy = nullptr;
   float *wx = nullptr, *wy = nullptr;
@@ -838,10 +838,10 @@ sllbm_status sllbm_precompute_departures(sllbm_ctx* c) {
     if (c->mt.valid) c->kernel = kKernelMapped;
   }
   c->q9_tma = 0;
-  if (c->kernel == kKernelQ9 && c->store == kStoreF32 && !mapped) {
+  if (c->kernel == kKernelQ9 && (c->store == kStoreF32 || c->store == kStoreBF16) && !mapped) {
     StepArgs a = step_args(c, c->state[0], c->state[1]);
     a.mapped = 0;
-    c->q9_tma = q9_tma_usable(a) ? 1 : 0;
+    c->q9_tma = q9_tma_usable(a, c->elem) ? 1 : 0;
   }
   c->ghost.on = (c->kernel == kKernelUniform || c->kernel == kKernelMapped || c->q9_tma) &&
                 (c->ax.periodic || c->ay.periodic);

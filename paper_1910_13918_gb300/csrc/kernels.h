@@ -49,8 +49,8 @@ struct StepArgs {
   // optional: (rho, u, v, theta) of each vertex's collision, dense [4][ny][nx] FP32 (plane
   // stride nv); null to skip
   float* mom;
-  // D2Q9, FP32 storage on a uniform grid: the TMA-staged kernel (the ghost cells hold the
-  // periodic images, kept by its writes); gx, gy, rows_alloc as in UniformTables
+  // D2Q9, FP32 or BF16 storage on a uniform grid: the TMA-staged kernel (the ghost cells hold
+  // the periodic images, kept by its writes); gx, gy, rows_alloc as in UniformTables
   int q9_tma;
   int gx, gy, rows_alloc;
 };
@@ -97,9 +97,10 @@ cudaError_t launch_step_plain_f64(const StepArgs& a, cudaStream_t s);
 // D2Q9 step (isothermal, one population, planar storage): FP32 arithmetic on FP32/BF16
 // deviations or FP64 on full populations; per-axis tables or, with a.mapped, descriptors.
 cudaError_t launch_step_q9(const StepArgs& a, int store, cudaStream_t s);
-// Whether the TMA-staged D2Q9 kernel can take this uniform grid (its window fits the shared
-// memory and the ghost cells); the host then keeps the periodic images in the ghost cells.
-bool q9_tma_usable(const StepArgs& a);
+// Whether the TMA-staged D2Q9 kernel can take this uniform grid with elem-byte storage (FP32 or
+// BF16: its window fits the shared memory and the ghost cells); the host then keeps the periodic
+// images in the ghost cells.
+bool q9_tma_usable(const StepArgs& a, int elem);
 
 // ---- precompute (FP64) ----
 struct GeomArgs {

@@ -443,40 +443,48 @@ __global__ void __launch_bounds__(kNT) step_q9_async_kernel(const __grid_constan
   if (!ok) atomicOr(a.flag, 1);
 }
 
-// FP32 storage on uniform grids, persistent CTAs with Tensor Memory Accelerator staging: a tile's
-// window of the 9 planes arrives as three tensor copies (cp.async.bulk.tensor, 3 planes each,
-// one mbarrier each), issued a whole tile ahead into the other of two buffers, so that the copies
-// of the next tile overlap the interpolation and collision of this one, and plane i's
+// FP32 or BF16 storage on uniform grids, persistent CTAs with Tensor Memory Accelerator staging:
+// a tile's window of the 9 planes arrives as three tensor copies (cp.async.bulk.tensor, 3 planes
+// each, one mbarrier each), issued a whole tile ahead into the other of two buffers, so that the
+// copies of the next tile overlap the interpolation and collision of this one, and plane i's
 // interpolation waits only for its own group.  The state's ghost cells hold the periodic images
 // (every write stores them too), so a window never wraps; its origin is rounded down to a
-// 16-byte boundary and the stencil offsets carry the remainder.
+// 16-byte boundary and the stencil offsets carry the remainder.  The interpolation runs in FP32
+// on the staged values of either storage type.
 constexpr int kQ9Groups = 3;   // tensor copies per tile (3 planes each)
 
 struct Q9Tma {
-  CUtensorMap tmap;   // 3D: (column, row, plane) over the whole allocation, FP32
-  int ox4;            // window origin relative to the tile origin, rounded down to 4 columns
-  int W4, H;          // window columns (a multiple of 4) and rows
-  int dx;             // ox - ox4: shift of the stencil offsets
+  CUtensorMap tmap;   // 3D: (column, row, plane) over the whole allocation, in the storage type
+  int oxa;            // window origin relative to the tile origin, rounded down to 16 bytes
+  int Wa, H;          // window columns (a multiple of 16 bytes) and rows
+  int dx;             // ox - oxa: shift of the stencil offsets
 };
 
-// floats of one copy group (3 planes of H x W4), padded to keep every copy 128-byte aligned
-__host__ __device__ inline int q9_group_elems(int W4, int H) { return (3 * H * W4 + 31) / 32 * 32; }
+// elements (of elem bytes) of one copy group (3 planes of H x Wa), padded to keep every copy
+// 128-byte aligned
+__host__ __device__ inline int q9_group_elems(int Wa, int H, int elem) {
+  return (3 * H * Wa * elem + 127) / 128 * 128 / elem;
+}
 
-size_t q9_tma_smem_bytes(int W4, int H) {
-  return 128 + sizeof(float) * (2 * (size_t)kQ9Groups * q9_group_elems(W4, H) + (size_t)kTY * W4) +
+size_t q9_tma_smem_bytes(int Wa, int H, int elem) {
+  return 128 + (size_t)elem * 2 * kQ9Groups * q9_group_elems(Wa, H, elem) + sizeof(float) * (size_t)kTY * Wa +
          sizeof(uint64_t) * 2 * kQ9Groups;
 }
 
-template <int P>
+__device__ __forceinline__ float q9_lds(const float* p) { return *p; }
+__device__ __forceinline__ float q9_lds(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+template <int P, typename Store>
 __global__ void __launch_bounds__(kNT) step_q9_tma_kernel(const __grid_constant__ StepArgs a,
                                                            const __grid_constant__ Window win,
                                                            const __grid_constant__ Q9Tma qt) {
   extern __shared__ unsigned char q9t_smem[];
-  float* base = reinterpret_cast<float*>(q9t_smem + ((128 - (smem_u32(q9t_smem) & 127)) & 127));
-  const int W4 = qt.W4, H = qt.H;
-  const int plane_elems = H * W4, group_elems = q9_group_elems(W4, H), buf_elems = kQ9Groups * group_elems;
-  float* S = base;                          // [2][3 groups][3][H][W4]
-  float* T = S + 2 * buf_elems;             // [kTY][W4]
+  Store* base = reinterpret_cast<Store*>(q9t_smem + ((128 - (smem_u32(q9t_smem) & 127)) & 127));
+  const int W4 = qt.Wa, H = qt.H;
+  const int plane_elems = H * W4, group_elems = q9_group_elems(W4, H, (int)sizeof(Store)),
+            buf_elems = kQ9Groups * group_elems;
+  Store* S = base;                                              // [2][3 groups][3][H][W4]
+  float* T = reinterpret_cast<float*>(S + 2 * buf_elems);       // [kTY][W4]
   uint64_t* BAR = reinterpret_cast<uint64_t*>(T + kTY * W4);   // [2][3]; offset a multiple of 8 B
   const int tid = threadIdx.x, lane = tid & 31, row = tid >> 5;
   const int tiles_x = (a.nx + 31) / 32;
@@ -493,8 +501,8 @@ __global__ void __launch_bounds__(kNT) step_q9_tma_kernel(const __grid_constant_
 #pragma unroll
     for (int g = 0; g < kQ9Groups; ++g) {
       uint64_t* bar = &BAR[buf * kQ9Groups + g];
-      mbar_expect_tx(bar, (unsigned)(sizeof(float) * 3 * plane_elems));
-      tma_load_3d(S + (size_t)buf * buf_elems + (size_t)g * group_elems, &qt.tmap, a.gx + tx0 + qt.ox4,
+      mbar_expect_tx(bar, (unsigned)(sizeof(Store) * 3 * plane_elems));
+      tma_load_3d(S + (size_t)buf * buf_elems + (size_t)g * group_elems, &qt.tmap, a.gx + tx0 + qt.oxa,
                   a.gy + ty0 + win.oy, 3 * g, bar);
     }
   };
@@ -523,7 +531,7 @@ __global__ void __launch_bounds__(kNT) step_q9_tma_kernel(const __grid_constant_
         yw[c][q] = a.wy[(size_t)(c * a.ny + yc) * (P + 1) + q];
       }
     }
-    const float* Sb = S + (size_t)buf * buf_elems;
+    const Store* Sb = S + (size_t)buf * buf_elems;
     float fb[kN];
 #pragma unroll
     for (int i = 0; i < kN; ++i) {
@@ -539,16 +547,16 @@ __global__ void __launch_bounds__(kNT) step_q9_tma_kernel(const __grid_constant_
             if (!mbar_wait(&BAR[(buf ^ 1) * kQ9Groups + g], (unsigned)(((k + 1) >> 1) & 1), a.flag)) return;
         return;
       }
-      const float* Si = Sb + (i / 3) * group_elems + (i % 3) * plane_elems;
+      const Store* Si = Sb + (i / 3) * group_elems + (i % 3) * plane_elems;
 #pragma unroll
       for (int m = 0; m < kCC; ++m) {
         const int c = lane + 32 * m;
         if (c < W4) {
-          const float* col = Si + yo[cb] * W4 + c;
-          const float b0 = col[0];
+          const Store* col = Si + yo[cb] * W4 + c;
+          const float b0 = q9_lds(col);
           float acc = b0;
 #pragma unroll
-          for (int q = 1; q <= P; ++q) acc = fmaf(yw[cb][q], col[q * W4] - b0, acc);
+          for (int q = 1; q <= P; ++q) acc = fmaf(yw[cb][q], q9_lds(col + q * W4) - b0, acc);
           T[row * W4 + c] = acc;
         }
       }
@@ -565,70 +573,75 @@ __global__ void __launch_bounds__(kNT) step_q9_tma_kernel(const __grid_constant_
     if (x < a.nx && y < a.ny) {
       const bool ok = collide_q9_f32(fb, a.cs, a.cp);
       if (!ok) atomicOr(a.flag, 1);
-      float* dst = static_cast<float*>(a.dst);
+      Store* dst = static_cast<Store*>(a.dst);
       store_images(a.ghost, x, y, [&](int xx, int yy) {
-        float* o = dst + (ptrdiff_t)yy * a.pitch + xx;
+        Store* o = dst + (ptrdiff_t)yy * a.pitch + xx;
 #pragma unroll
-        for (int i = 0; i < kN; ++i) o[(size_t)i * a.plane_stride] = fb[i];
+        for (int i = 0; i < kN; ++i) st_store(o + (size_t)i * a.plane_stride, fb[i]);
       });
     }
   }
 }
 
-// Window of the TMA kernel for a uniform grid, or false if the kernel cannot take it (the
-// window, rounded to 16-byte columns, must fit the shared memory and stay inside the ghost cells).
-bool q9_tma_window(const StepArgs& a, Window* win, Q9Tma* qt) {
-  if (a.mapped || a.xs != 1) return false;
+// Window of the TMA kernel for a uniform grid and elements of elem bytes, or false if the kernel
+// cannot take it (the window, rounded to 16-byte columns, must fit the shared memory and stay
+// inside the ghost cells).
+bool q9_tma_window(const StepArgs& a, int elem, Window* win, Q9Tma* qt) {
+  if (a.mapped || a.xs != 1 || (elem != 4 && elem != 2)) return false;
+  const int u = 16 / elem;   // columns of 16 bytes
   *win = Window{a.offx_min, a.offy_min, 32 + a.offx_max - a.offx_min, kTY + a.offy_max - a.offy_min};
-  const int ox4 = (win->ox >= 0) ? win->ox / 4 * 4 : -((-win->ox + 3) / 4 * 4);
-  qt->ox4 = ox4;
-  qt->dx = win->ox - ox4;
-  qt->W4 = (win->W + qt->dx + 3) / 4 * 4;
+  const int oxa = (win->ox >= 0) ? win->ox / u * u : -((-win->ox + u - 1) / u * u);
+  qt->oxa = oxa;
+  qt->dx = win->ox - oxa;
+  qt->Wa = (win->W + qt->dx + u - 1) / u * u;
   qt->H = win->H;
-  if (qt->W4 > kMaxW || qt->H > kMaxH || qt->H > 256) return false;
+  if (qt->Wa > kMaxW || qt->H > kMaxH || qt->H > 256) return false;
   // first and last window column / row of any tile, against the allocation's ghost cells
   const int tiles_x = (a.nx + 31) / 32, tiles_y = (a.ny + kTY - 1) / kTY;
-  if (ox4 < -a.gx || (tiles_x - 1) * 32 + ox4 + qt->W4 > a.pitch - a.gx) return false;
+  if (oxa < -a.gx || (tiles_x - 1) * 32 + oxa + qt->Wa > a.pitch - a.gx) return false;
   if (win->oy < -a.gy || (tiles_y - 1) * kTY + win->oy + qt->H > a.rows_alloc - a.gy) return false;
-  return q9_tma_smem_bytes(qt->W4, qt->H) <= 200 * 1024;
+  if ((a.gx * elem) % 16 != 0 || ((size_t)a.pitch * elem) % 16 != 0) return false;   // 16-byte copy origins
+  return q9_tma_smem_bytes(qt->Wa, qt->H, elem) <= 200 * 1024;
 }
 
-template <int P>
+template <int P, typename Store>
 static cudaError_t launch_q9_tma(const StepArgs& a, const Window& win, Q9Tma qt, cudaStream_t s) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  const float* alloc = static_cast<const float*>(a.src) - ((ptrdiff_t)a.gy * a.pitch + a.gx);
+  const Store* alloc = static_cast<const Store*>(a.src) - ((ptrdiff_t)a.gy * a.pitch + a.gx);
   const cuuint64_t dims[3] = {(cuuint64_t)a.pitch, (cuuint64_t)a.rows_alloc, (cuuint64_t)kN};
-  const cuuint64_t strides[2] = {(cuuint64_t)a.pitch * sizeof(float), (cuuint64_t)a.plane_stride * sizeof(float)};
-  const cuuint32_t box[3] = {(cuuint32_t)qt.W4, (cuuint32_t)qt.H, 3u};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.pitch * sizeof(Store), (cuuint64_t)a.plane_stride * sizeof(Store)};
+  const cuuint32_t box[3] = {(cuuint32_t)qt.Wa, (cuuint32_t)qt.H, 3u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
-  if (enc(&qt.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(alloc), dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+  const CUtensorMapDataType dt =
+      sizeof(Store) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  if (enc(&qt.tmap, dt, 3, const_cast<Store*>(alloc), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+      CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  const size_t smem = q9_tma_smem_bytes(qt.W4, qt.H);
-  cudaError_t e = cudaFuncSetAttribute(step_q9_tma_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = step_q9_tma_kernel<P, Store>;
+  const size_t smem = q9_tma_smem_bytes(qt.Wa, qt.H, (int)sizeof(Store));
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, n_sm = 0, per_sm = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_q9_tma_kernel<P>, kNT, smem)) != cudaSuccess)
-    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, smem)) != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const int ntiles = ((a.nx + 31) / 32) * ((a.ny + kTY - 1) / kTY);
   const int grid = ntiles < n_sm * per_sm ? ntiles : n_sm * per_sm;   // persistent CTAs
-  step_q9_tma_kernel<P><<<grid, kNT, smem, s>>>(a, win, qt);
+  kern<<<grid, kNT, smem, s>>>(a, win, qt);
   return cudaGetLastError();
 }
 
 template <int P, typename Store>
 cudaError_t launch_ps(const StepArgs& a, cudaStream_t s) {
-  if constexpr (std::is_same<Store, float>::value) {
+  if constexpr (!std::is_same<Store, double>::value) {
     if (a.q9_tma) {   // chosen (and the ghost images kept) by the host set-up
       Window win;
       Q9Tma qt;
-      if (!q9_tma_window(a, &win, &qt)) return cudaErrorNotSupported;
-      return launch_q9_tma<P>(a, win, qt, s);
+      if (!q9_tma_window(a, (int)sizeof(Store), &win, &qt)) return cudaErrorNotSupported;
+      return launch_q9_tma<P, Store>(a, win, qt, s);
     }
   }
   if constexpr (!std::is_same<Store, double>::value) {
@@ -672,10 +685,10 @@ cudaError_t launch_store(const StepArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-bool q9_tma_usable(const StepArgs& a) {
+bool q9_tma_usable(const StepArgs& a, int elem) {
   Window win;
   Q9Tma qt;
-  return q9_tma_window(a, &win, &qt);
+  return q9_tma_window(a, elem, &win, &qt);
 }
 
 cudaError_t launch_step_q9(const StepArgs& a, int store, cudaStream_t s) {
